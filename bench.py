@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the electron scattering self-energy Sigma^{<>} (Eq. 3) on one GB300.
+
+One step = one evaluation of Sigma^> and Sigma^< for the medium FinFET-shaped workload
+(Nkz=Nqz=5, NE=256, Nw=32, Na=512, Nb=4 chain neighbours, Norb=12, complex128,
+seed 1): every row of the hot path (stage inputs, the q/w-independent products, the
+(q, w) correlation, the FP64 reduction and the write of Sigma) runs inside the step.
+Inputs (3.0 GB of G plus Dt) are larger than the 129 MB L2, so no flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form mixed|fp64] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  Under torchrun each rank evaluates its own replica of
+the workload (replicas only: the single-instance path has no cross-GPU exchange), and
+`value` is all ranks' points over the slowest rank's time.  `--impl reference` times
+the CPU FP64 oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SSE atom-energy-kz points/s and fraction of roofline vs plain FP64; p50/p99"
+UNIT = "points/s"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (no measured FP64 peak is recorded)
+SPLIT_PRODUCTS = 3           # split-bf16 products per real product in the mixed form
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--form", choices=("auto", "mixed", "fp64"), default="auto")
+    ap.add_argument("--workload", choices=("medium", "tiny"), default="medium")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed steps of the plain FP64 form measured beside the mixed form")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1912_08810_gb300 import inputs
+    return {"medium": (inputs.MEDIUM, 1), "tiny": (inputs.TINY, 0)}[name]
+
+
+def config_dict(geo, name, form):
+    return {"workload": f"{name} SSE: Nkz=Nqz={geo.nkz}, NE={geo.ne}, Nw={geo.nw}, Na={geo.na}, "
+                        f"Nb={geo.nb} chain, Norb=12, complex128",
+            "form": form, "nkz": geo.nkz, "nqz": geo.nqz, "ne": geo.ne, "nw": geo.nw, "na": geo.na,
+            "nb": geo.nb, "norb": 12, "seed": workload(name)[1],
+            "l2": "inputs 3.0 GB > 129 MB L2, no flush", "parallelism": "replicas"}
+
+
+# --- clocks ------------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.path = None
+        self.uuid = device_uuid
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"error": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"error": "no samples"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# --- profile-derived traffic -------------------------------------------------------------
+
+def source_digest(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag, digest):
+    """DRAM bytes per launch recorded in profiles/<kernel_tag>*.md for this exact source."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.startswith(kernel_tag) or not fn.endswith(".md"):
+            continue
+        txt = open(os.path.join(pdir, fn)).read()
+        m_d = re.search(r"source_digest:\s*([0-9a-f]+)", txt)
+        m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        if m_d and m_t and m_d.group(1) == digest:
+            return float(m_t.group(1))
+    return None
+
+
+KERNEL_SOURCES = {
+    "fp64": ("sse_fp64_direct", ["paper_1912_08810_gb300/csrc/sse_fp64.cu"]),
+    "mixed": ("sse_mixed", ["paper_1912_08810_gb300/csrc/sse_mixed.cu"]),
+}
+
+
+# --- our arm ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(step, steps, warmup, world, stream, clocks=None):
+    """W warm-up steps, then K timed steps bracketed by barrier + synchronize; CUDA events
+    on the launching stream per step.  Returns (total_ms, per_step_ms)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        step()
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in evs], clk
+
+
+def pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1912_08810_gb300 import inputs, sse
+
+    world, rank, local = dist_setup(args)
+    name = args.workload
+    geo, seed = workload(name)
+    inst = inputs.make_instance(geo, seed)
+    dev = {k: torch.from_numpy(inst[k]).cuda().contiguous() for k in ("G_gt", "G_lt", "D_gt", "D_lt", "dH", "neigh")}
+    S = {s: torch.empty_like(dev["G_gt"]) for s in ("gt", "lt")}
+    stream = torch.cuda.current_stream()
+
+    def make_plan(mode):
+        return sse.Plan(dev["neigh"], dev["dH"], nkz=geo.nkz, nqz=geo.nqz, ne=geo.ne, nw=geo.nw, mode=mode)
+
+    form = args.form
+    plan = None
+    if form in ("auto", "mixed"):
+        try:
+            plan = make_plan("mixed")
+            form = "mixed"
+        except sse.SSEError:
+            if form == "mixed":
+                raise
+            form = "fp64"
+    if plan is None:
+        plan = make_plan("fp64")
+    info = plan.info()
+    points = geo.points()
+    flops_step = 2 * info.flops_per_sign
+
+    def step():
+        plan.execute(dev["G_gt"], dev["G_lt"], dev["D_gt"], dev["D_lt"], S["gt"], S["lt"], stream=stream)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    total_ms, per_step, clk = time_steps(step, args.steps, args.warmup, world, stream, clocks)
+    plan.status()
+    total_ms_max = max_over_ranks(total_ms, world)
+    value = points * args.steps * world / (total_ms_max / 1e3)
+    launches_per_step = 1
+    kern_ms = statistics.mean(per_step)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    tag, srcs = KERNEL_SOURCES[form]
+    digest = source_digest(srcs)
+    traffic = profiled_traffic(tag, digest)
+    if form == "mixed":
+        bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+        peak = bf16 / SPLIT_PRODUCTS
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_source": f"measured bf16 sustained {bf16} TFLOP/s / {SPLIT_PRODUCTS} split products"}
+    else:
+        peak = FP64_NOMINAL_TFLOPS
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (DFMA pipe)"}
+    achieved = flops_step / (kern_ms / 1e3) / 1e12
+    roof.update({"kernel": tag, "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": traffic, "algorithmic_flops_per_launch": flops_step,
+                 "algorithmic_bytes_per_launch": 2 * info.bytes_per_sign, "source_digest": digest})
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+           "p50_ms": pct(per_step, 50), "p99_ms": pct(per_step, 99),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16x3->f32->f64" if form == "mixed" else "f64",
+           "data": "synthetic (seeded numpy; G anti-Hermitian, Dt Hermitian, chain neighbours)",
+           "config": config_dict(geo, name, form), "roofline": roof, "clocks": clk,
+           "gpu_launches": launches_per_step * args.steps}
+
+    # the plain FP64 form on the same workload, for the "vs plain FP64" part of the metric
+    if form == "mixed" and args.fp64_steps > 0:
+        p64 = make_plan("fp64")
+
+        def step64():
+            p64.execute(dev["G_gt"], dev["G_lt"], dev["D_gt"], dev["D_lt"], S["gt"], S["lt"], stream=stream)
+
+        t64, ps64, _ = time_steps(step64, args.fp64_steps, 3, world, stream)
+        t64 = max_over_ranks(t64, world)
+        v64 = points * args.fp64_steps * world / (t64 / 1e3)
+        a64 = flops_step / (statistics.mean(ps64) / 1e3) / 1e12
+        out["fp64_form"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
+                            "roofline_frac": a64 / FP64_NOMINAL_TFLOPS, "speedup_of_value": value / v64}
+        p64.close()
+
+    if not args.no_e2e:
+        hostin = {k: torch.from_numpy(inst[k]).pin_memory() for k in ("G_gt", "G_lt", "D_gt", "D_lt")}
+        hostout = {s: torch.empty(S[s].shape, dtype=S[s].dtype).pin_memory() for s in ("gt", "lt")}
+
+        def step_e2e():
+            plan.execute_host(hostin["G_gt"], hostin["G_lt"], hostin["D_gt"], hostin["D_lt"],
+                              hostout["gt"], hostout["lt"], stream=stream)
+
+        step_e2e()
+        barrier(world)
+        k_e2e = max(1, min(args.steps, 3 if form == "fp64" else args.steps))
+        t = time.perf_counter()
+        for _ in range(k_e2e):
+            step_e2e()
+        e2e_s = max_over_ranks(time.perf_counter() - t, world)
+        h2d = sum(hostin[k].numel() * hostin[k].element_size() for k in hostin)
+        d2h = sum(hostout[s].numel() * hostout[s].element_size() for s in hostout)
+        out["e2e"] = {"value": points * k_e2e * world / e2e_s, "unit": UNIT, "steps": k_e2e,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "api": "sse_execute_host (pinned host buffers)"}
+        out["gpu_launches"] += k_e2e * launches_per_step + 1
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_sample(inst, geo)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_sample(inst, geo, n_atoms=None):
+    """Oracle on atoms [0, n) of the same workload, both signs; returns the baseline dict."""
+    import oracle
+    cores = oracle.num_threads()
+    n = n_atoms or max(4, cores)
+    t = time.perf_counter()
+    for s in ("gt", "lt"):
+        oracle.sigma_atoms(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], 0, n)
+    dt = time.perf_counter() - t
+    pts = geo.nkz * geo.ne * n
+    return {"value": pts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"atoms 0..{n - 1} x all (kz, E), both signs ({pts} points, {dt:.1f} s)"}
+
+
+# --- reference arm: the CPU FP64 oracle ---------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1912_08810_gb300 import inputs
+    name = args.workload
+    geo, seed = workload(name)
+    inst = inputs.make_instance(geo, seed)
+    cores = oracle.num_threads()
+    n = max(4, cores)
+
+    def step():
+        for s in ("gt", "lt"):
+            oracle.sigma_atoms(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], 0, n)
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t)
+    pts = geo.nkz * geo.ne * n
+    value = pts * len(times) / sum(times)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded numpy)", "config": config_dict(geo, name, "oracle"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"atoms 0..{n - 1} x all (kz, E), both signs per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,134 @@
+/*
+ * sse.h -- C ABI of the GB300 scattering self-energy library (libsse_gb300.so).
+ *
+ * The library evaluates the electron scattering self-energy of Eq. 3 (Section 2),
+ * after the pre-combination of the phonon Green's function described in Section 3
+ * ("Dataflow Optimizations", inputs list):
+ *
+ *   Sigma^s[k,E,a] = sum_{slot: f = neigh[a,slot] >= 0} sum_{i,j in x,y,z} sum_{q < nqz}
+ *                    sum_{w < nw, E' = E - (w + omega_first) >= 0}
+ *                    Dt^s[q,w,a,slot,i,j] * dH[a,slot,i] . G^s[(k-q) mod nkz, E', f] . dH[a,slot,j]^dagger
+ *
+ * for both signs s in {>, <}, on norb x norb complex blocks (norb = 12).  Readings of
+ * the paper fixed by this ABI:
+ *   - the prefactor i and the frequency weight of Eq. 3 are the caller's (factor 1);
+ *   - the sum index l of Eq. 3 is the neighbour slot;
+ *   - grad_j H_ba is the conjugate transpose of the stored dH[a,slot,j];
+ *   - kz - qz wraps modulo nkz; E - omega below the grid contributes 0;
+ *   - Sigma is overwritten, not accumulated.
+ *
+ * Layouts (row-major; complex = interleaved re/im, double2 for SSE_C128, float2 for
+ * SSE_C64; every array of one plan uses the plan's dtype):
+ *   G^s   [nkz][ne][na][12][12]       device, read-only
+ *   Dt^s  [nqz][nw][na][nb_max][3][3] device, read-only
+ *   dH    [na][nb_max][3][12][12]     device, read-only, borrowed by the plan
+ *   neigh [na][nb_max] int32          device, read-only, borrowed by the plan; -1 = empty slot
+ *   Sigma [nkz][ne][na][12][12]       device, written
+ *
+ * Ownership: the caller owns every buffer.  A plan borrows neigh and dH for its whole
+ * lifetime (they must not change after sse_plan; the neighbour list is validated
+ * once, at sse_plan).  A server ticket borrows its sse_io buffers until sse_poll
+ * returns a final status.  The library owns only its plans, their workspace and the
+ * server's queues.
+ *
+ * Errors: every entry point returns an sse_status; no C++ exception crosses the ABI,
+ * nothing aborts and no kernel traps.  sse_last_error() gives the calling thread's
+ * message for the last failure.  Kernels that wait on the device stop after a bounded
+ * time and record SSE_E_TIMEOUT in the plan's device status (see sse_plan_status).
+ *
+ * Streams are passed as `void *` holding a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef SSE_GB300_SSE_H
+#define SSE_GB300_SSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SSE_API __attribute__((visibility("default")))
+#else
+#define SSE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sse_status;
+enum {
+    SSE_OK = 0,
+    SSE_NOT_READY = 1,          /* sse_poll: the request is still queued or running */
+    SSE_E_INVALID_ARG = -1,     /* bad pointer, size, dtype, mode or neighbour index */
+    SSE_E_OUT_OF_MEMORY = -2,   /* a device or host allocation failed */
+    SSE_E_CUDA = -3,            /* a CUDA runtime call failed (message has the CUDA error) */
+    SSE_E_OVER_BUDGET = -4,     /* the request can never fit the server's memory budget */
+    SSE_E_TIMEOUT = -5,         /* a bounded device or host wait expired */
+    SSE_E_UNKNOWN_TICKET = -6,  /* sse_poll: no such ticket (or already collected) */
+    SSE_E_SHUTDOWN = -7,        /* the server is shutting down or was destroyed */
+    SSE_E_CANCELLED = -9        /* the request was cancelled before it ran */
+};
+
+typedef enum { SSE_C128 = 0, SSE_C64 = 1 } sse_dtype;
+
+/* SSE_MODE_FP64: every product and sum in FP64 (the oracle-matching reference form).
+ * SSE_MODE_MIXED: products on the tensor cores from split-bf16 operands with FP32
+ * accumulation, partial sums reduced into Sigma in FP64. */
+typedef enum { SSE_MODE_FP64 = 0, SSE_MODE_MIXED = 1 } sse_mode;
+
+typedef struct {
+    int32_t nkz, nqz, ne, nw, na, nb_max;
+    int32_t norb;         /* must be 12 */
+    int32_t omega_first;  /* w means (w + omega_first) energy-grid steps; >= 0 */
+    const int32_t *neigh; /* device [na][nb_max] */
+    const void *dH;       /* device [na][nb_max][3][12][12] */
+    int32_t dtype;        /* sse_dtype */
+    int32_t mode;         /* sse_mode */
+} sse_geometry;
+
+typedef struct {
+    const void *G_gt, *G_lt; /* device G^>, G^< */
+    const void *D_gt, *D_lt; /* device Dt^>, Dt^< */
+    void *S_gt, *S_lt;       /* device Sigma^>, Sigma^<; NULL skips that sign */
+} sse_io;
+
+typedef struct sse_plan_s sse_plan_t;
+typedef struct sse_server_s sse_server_t;
+
+typedef struct {
+    int32_t mode, dtype;
+    int64_t points;          /* nkz * ne * na output blocks per sign */
+    double flops_per_sign;   /* algorithmic real flops per sign (8 per complex MAC) */
+    double bytes_per_sign;   /* algorithmic HBM bytes per sign: read G, Dt, dH once, write Sigma */
+    int64_t workspace_bytes; /* device memory owned by the plan */
+    int32_t tile_e;          /* energies per tile of the chosen kernel */
+    int32_t kernel_id;       /* 0 = FP64 direct, 1 = mixed tensor-core */
+} sse_plan_info;
+
+/* Validate the geometry (copies neigh to the host once to range-check it: every entry
+ * in [-1, na)), choose the kernel and its tiles, and allocate the plan.  On success
+ * *out owns a plan that the caller frees with sse_plan_destroy. */
+SSE_API sse_status sse_plan(const sse_geometry *geo, sse_plan_t **out);
+SSE_API sse_status sse_plan_destroy(sse_plan_t *plan);
+SSE_API sse_status sse_plan_query(const sse_plan_t *plan, sse_plan_info *info);
+
+/* Enqueue Sigma^> and/or Sigma^< for one instance on `stream` (asynchronous, stream
+ * ordered).  io buffers must follow the plan's geometry and dtype. */
+SSE_API sse_status sse_execute(sse_plan_t *plan, const sse_io *io, void *stream);
+
+/* Same computation with HOST buffers (pageable or pinned): copies the inputs to
+ * plan-owned device staging on `stream`, runs, copies Sigma back and synchronises
+ * the stream before returning.  Staging is allocated on first use and kept. */
+SSE_API sse_status sse_execute_host(sse_plan_t *plan, const sse_io *host_io, void *stream);
+
+/* Synchronise the plan's last stream and read (then clear) the device status word that
+ * its kernels write: SSE_OK, or SSE_E_TIMEOUT if a bounded device wait expired. */
+SSE_API sse_status sse_plan_status(sse_plan_t *plan);
+
+SSE_API const char *sse_status_string(sse_status status);
+SSE_API const char *sse_last_error(void);
+SSE_API int32_t sse_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSE_GB300_SSE_H */

@@ -1,0 +1,274 @@
+// C ABI of libsse_gb300.so: argument checks, plans, dispatch to the kernels.
+// The operation and the readings of the paper it fixes are documented in include/sse.h.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sse_internal.h"
+
+namespace sse {
+
+static thread_local std::string t_error;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_error = buf;
+}
+
+sse_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return SSE_E_CUDA;
+}
+
+double algorithmic_cmacs(const Dims &d, const std::vector<int32_t> &neigh) {
+    int64_t bonds = 0;
+    for (int32_t f : neigh) bonds += f >= 0;
+    int64_t valid_w = 0;  // sum_w max(0, ne - (w + omega_first))
+    for (int w = 0; w < d.nw; ++w) {
+        const int64_t v = (int64_t)d.ne - (w + d.omega_first);
+        valid_w += v > 0 ? v : 0;
+    }
+    const double products = (double)bonds * d.nkz * d.ne * 12.0 * kNorb * kNorb * kNorb;  // M_ij once per (k', E')
+    const double corr = (double)bonds * d.nkz * d.nqz * 9.0 * kBlk * (double)valid_w;      // sum over valid (q, w)
+    return products + corr;
+}
+
+// True when `ptr` is memory a kernel of the current device can dereference.
+static bool device_pointer(const void *ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static sse_status check_geometry(const sse_geometry *g) {
+    if (!g) return set_error("geometry is NULL"), SSE_E_INVALID_ARG;
+    if (g->nkz <= 0 || g->nqz <= 0 || g->ne <= 0 || g->nw <= 0 || g->na <= 0 || g->nb_max <= 0) {
+        set_error("sizes must be positive (nkz=%d nqz=%d ne=%d nw=%d na=%d nb_max=%d)", g->nkz, g->nqz, g->ne,
+                  g->nw, g->na, g->nb_max);
+        return SSE_E_INVALID_ARG;
+    }
+    if (g->norb != kNorb) return set_error("norb must be 12 (got %d)", g->norb), SSE_E_INVALID_ARG;
+    if (g->omega_first < 0) return set_error("omega_first must be >= 0"), SSE_E_INVALID_ARG;
+    if (g->dtype != SSE_C128 && g->dtype != SSE_C64) return set_error("unknown dtype %d", g->dtype), SSE_E_INVALID_ARG;
+    if (g->mode != SSE_MODE_FP64 && g->mode != SSE_MODE_MIXED)
+        return set_error("unknown mode %d", g->mode), SSE_E_INVALID_ARG;
+    if ((int64_t)g->nkz * g->ne * g->na > (int64_t)1 << 40) return set_error("problem too large"), SSE_E_INVALID_ARG;
+    if (!device_pointer(g->neigh)) return set_error("neigh is not a device pointer"), SSE_E_INVALID_ARG;
+    if (!device_pointer(g->dH)) return set_error("dH is not a device pointer"), SSE_E_INVALID_ARG;
+    return SSE_OK;
+}
+
+static sse_status check_io(const Plan &p, const sse_io *io) {
+    if (!io) return set_error("io is NULL"), SSE_E_INVALID_ARG;
+    if (!io->S_gt && !io->S_lt) return SSE_OK;
+    if (io->S_gt && (!device_pointer(io->G_gt) || !device_pointer(io->D_gt) || !device_pointer(io->S_gt)))
+        return set_error("G_gt, D_gt and S_gt must be device pointers"), SSE_E_INVALID_ARG;
+    if (io->S_lt && (!device_pointer(io->G_lt) || !device_pointer(io->D_lt) || !device_pointer(io->S_lt)))
+        return set_error("G_lt, D_lt and S_lt must be device pointers"), SSE_E_INVALID_ARG;
+    (void)p;
+    return SSE_OK;
+}
+
+}  // namespace sse
+
+using namespace sse;
+
+struct sse_plan_s : public Plan {
+    std::vector<int32_t> neigh_host;
+    double cmacs_per_sign = 0.0;
+};
+
+extern "C" {
+
+int32_t sse_abi_version(void) { return 1; }
+
+const char *sse_last_error(void) { return t_error.c_str(); }
+
+const char *sse_status_string(sse_status s) {
+    switch (s) {
+        case SSE_OK: return "SSE_OK";
+        case SSE_NOT_READY: return "SSE_NOT_READY";
+        case SSE_E_INVALID_ARG: return "SSE_E_INVALID_ARG";
+        case SSE_E_OUT_OF_MEMORY: return "SSE_E_OUT_OF_MEMORY";
+        case SSE_E_CUDA: return "SSE_E_CUDA";
+        case SSE_E_OVER_BUDGET: return "SSE_E_OVER_BUDGET";
+        case SSE_E_TIMEOUT: return "SSE_E_TIMEOUT";
+        case SSE_E_UNKNOWN_TICKET: return "SSE_E_UNKNOWN_TICKET";
+        case SSE_E_SHUTDOWN: return "SSE_E_SHUTDOWN";
+        case SSE_E_CANCELLED: return "SSE_E_CANCELLED";
+        default: return "SSE_E_UNKNOWN_STATUS";
+    }
+}
+
+sse_status sse_plan(const sse_geometry *geo, sse_plan_t **out) {
+    if (!out) return set_error("out is NULL"), SSE_E_INVALID_ARG;
+    *out = nullptr;
+    sse_status st = check_geometry(geo);
+    if (st != SSE_OK) return st;
+    sse_plan_s *p = new (std::nothrow) sse_plan_s();
+    if (!p) return set_error("host allocation failed"), SSE_E_OUT_OF_MEMORY;
+    p->geo = *geo;
+    p->d = Dims{geo->nkz, geo->nqz, geo->ne, geo->nw, geo->na, geo->nb_max, geo->omega_first};
+    cudaGetDevice(&p->device);
+    const size_t nn = (size_t)geo->na * geo->nb_max;
+    try {
+        p->neigh_host.resize(nn);
+    } catch (...) {
+        delete p;
+        return set_error("host allocation failed"), SSE_E_OUT_OF_MEMORY;
+    }
+    cudaError_t e = cudaMemcpy(p->neigh_host.data(), geo->neigh, nn * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "copy neigh to host");
+    }
+    for (size_t i = 0; i < nn; ++i) {
+        const int32_t f = p->neigh_host[i];
+        if (f < -1 || f >= geo->na) {
+            set_error("neigh[%zu][%zu] = %d is outside [-1, %d)", i / geo->nb_max, i % geo->nb_max, f, geo->na);
+            delete p;
+            return SSE_E_INVALID_ARG;
+        }
+    }
+    p->cmacs_per_sign = algorithmic_cmacs(p->d, p->neigh_host);
+    e = cudaMalloc(&p->d_status, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        delete p;
+        return e == cudaErrorMemoryAllocation ? (set_error("cudaMalloc status word"), SSE_E_OUT_OF_MEMORY)
+                                              : cuda_fail(e, "cudaMalloc status word");
+    }
+    cudaMemset(p->d_status, 0, sizeof(int32_t));
+    p->workspace_bytes = sizeof(int32_t);
+    if (geo->mode == SSE_MODE_MIXED) {
+        p->kernel_id = 1;
+        st = mixed_plan_init(*p);
+        if (st != SSE_OK) {
+            cudaFree(p->d_status);
+            delete p;
+            return st;
+        }
+    } else {
+        p->kernel_id = 0;
+        p->tile_e = 1;
+    }
+    *out = p;
+    return SSE_OK;
+}
+
+sse_status sse_plan_destroy(sse_plan_t *plan) {
+    if (!plan) return SSE_OK;
+    if (plan->last_stream) cudaStreamSynchronize(plan->last_stream);
+    mixed_plan_free(*plan);
+    if (plan->d_status) cudaFree(plan->d_status);
+    if (plan->staging) cudaFree(plan->staging);
+    delete plan;
+    return SSE_OK;
+}
+
+sse_status sse_plan_query(const sse_plan_t *plan, sse_plan_info *info) {
+    if (!plan || !info) return set_error("plan or info is NULL"), SSE_E_INVALID_ARG;
+    const Dims &d = plan->d;
+    const double eb = (double)elem_bytes(plan->geo.dtype);
+    info->mode = plan->geo.mode;
+    info->dtype = plan->geo.dtype;
+    info->points = (int64_t)d.nkz * d.ne * d.na;
+    info->flops_per_sign = 8.0 * plan->cmacs_per_sign;
+    info->bytes_per_sign = eb * (2.0 * g_elems(d) + d_elems(d) + 0.5 * dh_elems(d)) + 0.5 * 4.0 * d.na * d.nb;
+    info->workspace_bytes = plan->workspace_bytes + (int64_t)plan->staging_bytes;
+    info->tile_e = plan->tile_e;
+    info->kernel_id = plan->kernel_id;
+    return SSE_OK;
+}
+
+static sse_status dispatch(sse_plan_t *plan, const sse_io &io, cudaStream_t st) {
+    plan->last_stream = st;
+    if (plan->kernel_id == 1) return launch_mixed(*plan, io, st);
+    return launch_fp64_direct(*plan, io, st);
+}
+
+sse_status sse_execute(sse_plan_t *plan, const sse_io *io, void *stream) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    sse_status st = check_io(*plan, io);
+    if (st != SSE_OK) return st;
+    return dispatch(plan, *io, (cudaStream_t)stream);
+}
+
+sse_status sse_execute_host(sse_plan_t *plan, const sse_io *h, void *stream) {
+    if (!plan || !h) return set_error("plan or io is NULL"), SSE_E_INVALID_ARG;
+    const Dims &d = plan->d;
+    const size_t eb = elem_bytes(plan->geo.dtype);
+    const size_t gb = g_elems(d) * eb, db = d_elems(d) * eb;
+    const bool sgn[2] = {h->S_gt != nullptr, h->S_lt != nullptr};
+    const void *hg[2] = {h->G_gt, h->G_lt}, *hd[2] = {h->D_gt, h->D_lt};
+    void *hs[2] = {h->S_gt, h->S_lt};
+    for (int s = 0; s < 2; ++s)
+        if (sgn[s] && (!hg[s] || !hd[s])) return set_error("missing host input for a requested sign"), SSE_E_INVALID_ARG;
+    const size_t need = 2 * (2 * gb + db);  // per sign: G, Dt, Sigma
+    if (plan->staging_bytes < need) {
+        if (plan->staging) cudaFree(plan->staging);
+        plan->staging = nullptr;
+        plan->staging_bytes = 0;
+        cudaError_t e = cudaMalloc(&plan->staging, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error("cudaMalloc of %zu staging bytes failed", need), SSE_E_OUT_OF_MEMORY;
+        }
+        plan->staging_bytes = need;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    char *base = (char *)plan->staging;
+    sse_io dio{};
+    const void **dg[2] = {&dio.G_gt, &dio.G_lt}, **dd[2] = {&dio.D_gt, &dio.D_lt};
+    void **ds[2] = {&dio.S_gt, &dio.S_lt};
+    for (int s = 0; s < 2; ++s) {
+        if (!sgn[s]) continue;
+        char *g = base + s * (2 * gb + db), *dt = g + gb, *sg = dt + db;
+        cudaError_t e = cudaMemcpyAsync(g, hg[s], gb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dt, hd[s], db, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy inputs to the device");
+        *dg[s] = g;
+        *dd[s] = dt;
+        *ds[s] = sg;
+    }
+    sse_status rs = dispatch(plan, dio, st);
+    if (rs != SSE_OK) return rs;
+    for (int s = 0; s < 2; ++s) {
+        if (!sgn[s]) continue;
+        cudaError_t e = cudaMemcpyAsync(hs[s], *ds[s], gb, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy Sigma to the host");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise after sse_execute_host");
+    return SSE_OK;
+}
+
+sse_status sse_plan_status(sse_plan_t *plan) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    cudaError_t e = plan->last_stream ? cudaStreamSynchronize(plan->last_stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise plan stream");
+    int32_t v = 0;
+    e = cudaMemcpy(&v, plan->d_status, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read plan status");
+    if (v != 0) {
+        cudaMemset(plan->d_status, 0, sizeof v);
+        set_error("a device-side wait of this plan expired (code %d)", v);
+        return SSE_E_TIMEOUT;
+    }
+    return SSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+// Internal declarations shared by the translation units of libsse_gb300.so.
+// Nothing here is part of the C ABI (include/sse.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sse.h"
+
+namespace sse {
+
+constexpr int kNorb = 12;             // orbitals per atom (the only size the kernels take)
+constexpr int kBlk = kNorb * kNorb;   // complex values per norb x norb block
+constexpr int kN3D = 3;               // vibration directions i, j
+
+// Sizes of one instance (Table 1 symbols) in the form the kernels take.
+struct Dims {
+    int32_t nkz, nqz, ne, nw, na, nb, omega_first;
+};
+
+struct Plan {
+    sse_geometry geo{};
+    Dims d{};
+    int device = 0;
+    int kernel_id = 0;
+    int tile_e = 1;
+    int32_t *d_status = nullptr;      // device status word written by kernels with bounded waits
+    void *staging = nullptr;          // device staging of sse_execute_host
+    size_t staging_bytes = 0;
+    cudaStream_t last_stream = nullptr;
+    int64_t workspace_bytes = 0;
+    // Mixed-path workspace (see sse_mixed.cu)
+    void *mixed_ws = nullptr;
+    size_t mixed_ws_bytes = 0;
+};
+
+// Thread-local error message for sse_last_error().
+void set_error(const char *fmt, ...);
+sse_status cuda_fail(cudaError_t e, const char *what);
+
+inline size_t elem_bytes(int dtype) { return dtype == SSE_C128 ? 16 : 8; }
+inline size_t g_elems(const Dims &d) { return (size_t)d.nkz * d.ne * d.na * kBlk; }
+inline size_t d_elems(const Dims &d) { return (size_t)d.nqz * d.nw * d.na * d.nb * kN3D * kN3D; }
+inline size_t dh_elems(const Dims &d) { return (size_t)d.na * d.nb * kN3D * kBlk; }
+
+// Algorithmic work per sign (complex MACs): the q/w-independent products once per
+// (k', E', a, slot) plus the correlation over the valid (q, w).
+double algorithmic_cmacs(const Dims &d, const std::vector<int32_t> &neigh_host);
+
+// Kernel launchers (return SSE_OK or an error after set_error).
+sse_status launch_fp64_direct(const Plan &p, const sse_io &io, cudaStream_t st);
+sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st);
+sse_status mixed_plan_init(Plan &p);
+void mixed_plan_free(Plan &p);
+
+}  // namespace sse

@@ -88,7 +88,7 @@ def _anti_hermitian_blocks(rng, lead_shape, norb) -> np.ndarray:
 
 def _hermitian_3x3(rng, lead_shape) -> np.ndarray:
     b = _complex_normal(rng, tuple(lead_shape) + (N3D, N3D))
-    return b + np.conj(np.swapaxes(b, -1, -2))
+    return np.ascontiguousarray(b + np.conj(np.swapaxes(b, -1, -2)))
 
 
 def make_instance(geo: Geometry, seed: int, *, dtype=np.complex128,
@@ -119,9 +119,8 @@ def make_instance(geo: Geometry, seed: int, *, dtype=np.complex128,
     d_gt = _hermitian_3x3(rng, lead_d)
     d_lt = _hermitian_3x3(rng, lead_d)
     out = dict(G_gt=g_gt, G_lt=g_lt, D_gt=d_gt, D_lt=d_lt, dH=dh, neigh=neigh)
-    if np.dtype(dtype) != np.complex128:
-        for k in ("G_gt", "G_lt", "D_gt", "D_lt", "dH"):
-            out[k] = out[k].astype(dtype)
+    for k in ("G_gt", "G_lt", "D_gt", "D_lt", "dH"):
+        out[k] = np.ascontiguousarray(out[k], dtype=dtype)
     return out
 
 

@@ -1,0 +1,234 @@
+"""ctypes binding of libsse_gb300.so -- argument marshalling only.
+
+The functions here carry the C ABI's names (include/sse.h) and do no arithmetic: every
+step of the self-energy runs in the CUDA library.  If the library is missing the import
+of a function fails loudly; there is no CPU fallback.
+
+``Plan`` is a convenience wrapper that takes torch tensors (PyTorch supplies device
+memory and streams only) and passes their device pointers to the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsse_gb300.so")
+
+SSE_OK = 0
+SSE_NOT_READY = 1
+SSE_E_INVALID_ARG = -1
+SSE_E_OUT_OF_MEMORY = -2
+SSE_E_CUDA = -3
+SSE_E_OVER_BUDGET = -4
+SSE_E_TIMEOUT = -5
+SSE_E_UNKNOWN_TICKET = -6
+SSE_E_SHUTDOWN = -7
+SSE_E_CANCELLED = -9
+
+SSE_C128 = 0
+SSE_C64 = 1
+SSE_MODE_FP64 = 0
+SSE_MODE_MIXED = 1
+
+# Every function include/sse.h declares (checked by the CPU test suite).
+EXPORTED = (
+    "sse_plan", "sse_plan_destroy", "sse_plan_query", "sse_execute", "sse_execute_host",
+    "sse_plan_status", "sse_status_string", "sse_last_error", "sse_abi_version",
+)
+
+
+class sse_geometry(ctypes.Structure):
+    _fields_ = [("nkz", ctypes.c_int32), ("nqz", ctypes.c_int32), ("ne", ctypes.c_int32),
+                ("nw", ctypes.c_int32), ("na", ctypes.c_int32), ("nb_max", ctypes.c_int32),
+                ("norb", ctypes.c_int32), ("omega_first", ctypes.c_int32),
+                ("neigh", ctypes.c_void_p), ("dH", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+class sse_io(ctypes.Structure):
+    _fields_ = [("G_gt", ctypes.c_void_p), ("G_lt", ctypes.c_void_p),
+                ("D_gt", ctypes.c_void_p), ("D_lt", ctypes.c_void_p),
+                ("S_gt", ctypes.c_void_p), ("S_lt", ctypes.c_void_p)]
+
+
+class sse_plan_info(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("dtype", ctypes.c_int32), ("points", ctypes.c_int64),
+                ("flops_per_sign", ctypes.c_double), ("bytes_per_sign", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_int64), ("tile_e", ctypes.c_int32),
+                ("kernel_id", ctypes.c_int32)]
+
+
+class SSEError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {status_name(status)} ({status}): {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load the CUDA library once; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(p)
+        vp, st = ctypes.c_void_p, ctypes.c_int32
+        sig = {
+            "sse_plan": ([ctypes.POINTER(sse_geometry), ctypes.POINTER(vp)], st),
+            "sse_plan_destroy": ([vp], st),
+            "sse_plan_query": ([vp, ctypes.POINTER(sse_plan_info)], st),
+            "sse_execute": ([vp, ctypes.POINTER(sse_io), vp], st),
+            "sse_execute_host": ([vp, ctypes.POINTER(sse_io), vp], st),
+            "sse_plan_status": ([vp], st),
+            "sse_status_string": ([st], ctypes.c_char_p),
+            "sse_last_error": ([], ctypes.c_char_p),
+            "sse_abi_version": ([], st),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes, fn.restype = args, res
+        _lib = lib
+        return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().sse_status_string(status).decode()
+    except Exception:  # library missing: still format the error
+        return str(status)
+
+
+def sse_last_error() -> str:
+    return load().sse_last_error().decode()
+
+
+def _check(status: int, where: str) -> int:
+    if status < 0:
+        raise SSEError(status, where, sse_last_error())
+    return status
+
+
+def sse_plan(geo: sse_geometry) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().sse_plan(ctypes.byref(geo), ctypes.byref(h)), "sse_plan")
+    return h
+
+
+def sse_plan_destroy(plan) -> None:
+    _check(load().sse_plan_destroy(plan), "sse_plan_destroy")
+
+
+def sse_plan_query(plan) -> sse_plan_info:
+    info = sse_plan_info()
+    _check(load().sse_plan_query(plan, ctypes.byref(info)), "sse_plan_query")
+    return info
+
+
+def sse_execute(plan, io: sse_io, stream: int = 0) -> None:
+    _check(load().sse_execute(plan, ctypes.byref(io), ctypes.c_void_p(stream)), "sse_execute")
+
+
+def sse_execute_host(plan, io: sse_io, stream: int = 0) -> None:
+    _check(load().sse_execute_host(plan, ctypes.byref(io), ctypes.c_void_p(stream)), "sse_execute_host")
+
+
+def sse_plan_status(plan) -> None:
+    _check(load().sse_plan_status(plan), "sse_plan_status")
+
+
+def sse_status_string(status: int) -> str:
+    return load().sse_status_string(status).decode()
+
+
+def sse_abi_version() -> int:
+    return int(load().sse_abi_version())
+
+
+# --- torch convenience wrapper (pointers and streams only) ----------------------------
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+class Plan:
+    """A plan over device tensors: neigh int32 [na, nb], dH complex [na, nb, 3, 12, 12].
+
+    ``mode`` is "fp64" or "mixed"; the dtype follows dH (complex128 or complex64).
+    """
+
+    def __init__(self, neigh, dH, *, nkz: int, nqz: int, ne: int, nw: int,
+                 omega_first: int = 1, mode: str = "fp64"):
+        import torch
+        if not (neigh.is_cuda and dH.is_cuda):
+            raise ValueError("neigh and dH must be CUDA tensors")
+        if not (neigh.is_contiguous() and dH.is_contiguous()):
+            raise ValueError("neigh and dH must be contiguous")
+        if neigh.dtype != torch.int32:
+            raise ValueError("neigh must be int32")
+        dtype = {torch.complex128: SSE_C128, torch.complex64: SSE_C64}.get(dH.dtype)
+        if dtype is None:
+            raise ValueError("dH must be complex128 or complex64")
+        na, nb = neigh.shape
+        if tuple(dH.shape) != (na, nb, 3, 12, 12):
+            raise ValueError(f"dH shape {tuple(dH.shape)} != {(na, nb, 3, 12, 12)}")
+        self.neigh, self.dH = neigh, dH  # kept alive: the plan borrows them
+        self.torch_dtype = dH.dtype
+        self.shape_g = (nkz, ne, na, 12, 12)
+        self.shape_d = (nqz, nw, na, nb, 3, 3)
+        self.geo = sse_geometry(nkz, nqz, ne, nw, na, nb, 12, omega_first, _ptr(neigh), _ptr(dH),
+                                dtype, SSE_MODE_MIXED if mode == "mixed" else SSE_MODE_FP64)
+        self.handle = sse_plan(self.geo)
+
+    def info(self) -> sse_plan_info:
+        return sse_plan_query(self.handle)
+
+    def _io(self, G_gt, G_lt, D_gt, D_lt, S_gt, S_lt) -> sse_io:
+        for t, shp in ((G_gt, self.shape_g), (G_lt, self.shape_g), (S_gt, self.shape_g),
+                       (S_lt, self.shape_g), (D_gt, self.shape_d), (D_lt, self.shape_d)):
+            if t is None:
+                continue
+            if tuple(t.shape) != shp or t.dtype != self.torch_dtype or not t.is_contiguous():
+                raise ValueError(f"tensor mismatch: shape {tuple(t.shape)} dtype {t.dtype} contiguous {t.is_contiguous()}; want shape {shp} dtype {self.torch_dtype}, contiguous")
+        return sse_io(_ptr(G_gt), _ptr(G_lt), _ptr(D_gt), _ptr(D_lt), _ptr(S_gt), _ptr(S_lt))
+
+    def execute(self, G_gt=None, G_lt=None, D_gt=None, D_lt=None, S_gt=None, S_lt=None,
+                stream=None) -> None:
+        import torch
+        for t in (G_gt, G_lt, D_gt, D_lt, S_gt, S_lt):
+            if t is not None and not t.is_cuda:
+                raise ValueError("execute() takes CUDA tensors; use execute_host() for host arrays")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sse_execute(self.handle, self._io(G_gt, G_lt, D_gt, D_lt, S_gt, S_lt), s.cuda_stream)
+
+    def execute_host(self, G_gt=None, G_lt=None, D_gt=None, D_lt=None, S_gt=None, S_lt=None,
+                     stream=None) -> None:
+        """Host tensors in and out (pinned or pageable); synchronous."""
+        import torch
+        for t in (G_gt, G_lt, D_gt, D_lt, S_gt, S_lt):
+            if t is not None and t.is_cuda:
+                raise ValueError("execute_host() takes host tensors")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sse_execute_host(self.handle, self._io(G_gt, G_lt, D_gt, D_lt, S_gt, S_lt), s.cuda_stream)
+
+    def status(self) -> None:
+        sse_plan_status(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            sse_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -57,3 +57,10 @@ def test_batched_subset_matches_full_draw():
     for k in ("G_gt", "D_lt", "dH", "neigh"):
         assert np.array_equal(full[2][k], one[k])
     assert full[0]["G_gt"].dtype == np.complex64
+
+
+def test_every_array_is_c_contiguous():
+    for dt in (np.complex128, np.complex64):
+        inst = inputs.make_instance(inputs.TINY, 2, dtype=dt)
+        for k in ("G_gt", "G_lt", "D_gt", "D_lt", "dH", "neigh"):
+            assert inst[k].flags.c_contiguous, k
