@@ -1,16 +1,644 @@
-// Mixed-precision tensor-core form (placeholder until the tcgen05 kernel lands).
+// Mixed-precision tensor-core form of the electron scattering self-energy (Eq. 3).
+//
+// Regrouping used here (exact by linearity; Section 3 "Dataflow Optimizations" removes
+// the (qz, w)-independent products from the correlation in the same spirit):
+//   X_i[k', E']  = dH_i . G[k', E', f]                          (per slot b, f = neigh[a, b])
+//   V_j[k, E]    = sum_{i, q, w} Dt_ij[q, w] X_i[(k-q) mod Nkz, E - w - omega_first]
+//   Sigma[k, E] += sum_j V_j[k, E] . dH_j^dagger                (reduced over slots in FP64)
+// The correlation is the dominant work.  It runs on the tensor cores (tcgen05, kind::f16)
+// as a Toeplitz-in-E, circulant-in-k contraction (the matrix form of Section 3's nested
+// map substitution):
+//   rows m = (e, k, j) of a tile of TE energies (3 * Nkz * TE <= 128),
+//   K     = (energy slot E' of the tile's window, i, k', re/im of X),
+//   N     = the 144 channels (r, t) of a 12 x 12 block,
+// with two TMEM accumulators (real and imaginary part of V).  A holds the Toeplitz
+// operand built from the folded Dt, B the X slices.  Both are split into bf16 hi + lo
+// and contracted as hi*hi + hi*lo + lo*hi with FP32 accumulation; the products
+// dH_i . G and V . dH^dagger run in FP32 on the CUDA cores; the sum over neighbour slots
+// is FP64.  G blocks arrive by bulk (TMA) copies into shared memory.
+//
+// Structure of one CTA (sign, atom a, range of tiles): for every (tile, slot) "job",
+// stream the tile's window of energy slots in stages (double-buffered): convert the
+// stage's G blocks, build the X slices and the Toeplitz slice in shared memory, issue the
+// MMAs from one thread and let them run while the next stage is built; at the end of the
+// job, drain the accumulators and apply dH_j^dagger.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
 #include "sse_internal.h"
+#include "tc_ptx.h"
 
 namespace sse {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 256;
+constexpr int kRowsMax = 128;    // MMA M
+constexpr int kCh = 144;         // MMA N: channels of a 12 x 12 block
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAccIm = 256; // TMEM column of the imaginary accumulator
+constexpr uint64_t kWaitNs = 250000000ull;  // bound on every device-side wait (0.25 s)
+constexpr int kMaxSlots = 32;
+constexpr int kVStride = 73;     // row stride (floats) of the drained accumulator tile
+
+// Compile-time tile geometry for a given Nkz.
+template <int NK>
+struct Geo {
+    static constexpr int KS = ((6 * NK + 7) / 8) * 8;  // K values per energy slot (i, k', re/im), padded
+    static constexpr int P = (KS % 16 == 0) ? 1 : 2;   // energy slots per stage (stage K multiple of 16)
+    static constexpr int KST = P * KS;                 // K per stage
+    static constexpr int TE = kRowsMax / (3 * NK);     // energies per tile
+    static constexpr int ROWS = 3 * NK * TE;           // used MMA rows
+    static constexpr int SBO_B = (KST / 8) * 128;      // bytes between 8-row groups of B
+    static constexpr int B_PLANE = (kCh / 8) * SBO_B;
+    static constexpr int SBO_A = (KST / 8) * 128;
+    static constexpr int A_PLANE = (kRowsMax / 8) * SBO_A;
+};
+
+struct MixParams {
+    const int32_t *neigh;
+    const void *dH;
+    const void *G[2];
+    const void *D[2];
+    void *S[2];
+    int32_t *status;
+    Dims d;
+    int nst;            // stages per job
+    int ntiles;         // tiles per atom
+    int tiles_per_cta;
+    int nchunks;        // CTAs per (sign, atom)
+    uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, g_stage;
+};
+
+__device__ __forceinline__ float2 cmul_conj_acc(float2 acc, float2 v, float2 h) {
+    // acc + v * conj(h)
+    acc.x = fmaf(v.x, h.x, acc.x);
+    acc.x = fmaf(v.y, h.y, acc.x);
+    acc.y = fmaf(v.y, h.x, acc.y);
+    acc.y = fmaf(-v.x, h.y, acc.y);
+    return acc;
+}
+
+template <typename CT>
+__device__ __forceinline__ void rmw_store(CT *dst, float2 v, bool first);
+template <>
+__device__ __forceinline__ void rmw_store<double2>(double2 *dst, float2 v, bool first) {
+    double2 o = make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
+    if (!first) {
+        const double2 old = *dst;
+        o.x += old.x;
+        o.y += old.y;
+    }
+    *dst = o;
+}
+template <>
+__device__ __forceinline__ void rmw_store<float2>(float2 *dst, float2 v, bool first) {
+    if (first) {
+        *dst = v;
+        return;
+    }
+    const float2 old = *dst;
+    const double x = f32_to_f64(old.x) + f32_to_f64(v.x);
+    const double y = f32_to_f64(old.y) + f32_to_f64(v.y);
+    *dst = make_float2(f64_to_f32(x), f64_to_f32(y));
+}
+
+template <int NK, typename CT>
+__global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams prm) {
+    using GG = Geo<NK>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const Dims d = prm.d;
+    const int sign = blockIdx.y;
+    const CT *__restrict__ G = (const CT *)prm.G[sign];
+    const CT *__restrict__ D = (const CT *)prm.D[sign];
+    CT *__restrict__ S = (CT *)prm.S[sign];
+    const CT *__restrict__ dH = (const CT *)prm.dH;
+    const int a = blockIdx.x / prm.nchunks, chunk = blockIdx.x % prm.nchunks;
+    const int t_begin = chunk * prm.tiles_per_cta;
+    const int t_end = min(prm.ntiles, t_begin + prm.tiles_per_cta);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nw = d.nw;
+    const int omega_max = d.omega_first + nw - 1;
+
+    uint8_t *sB = smem + prm.off_b;                 // [2 stages][hi, lo] B planes
+    uint8_t *sA = smem + prm.off_a;                 // [2 stages][re, im][hi, lo] A planes
+    uint8_t *sG = smem + prm.off_g;                 // [2 stages] raw G blocks
+    uint32_t *sDf = (uint32_t *)(smem + prm.off_df);  // [k][k'][w][ij][re, im] split words
+    float2 *sDh = (float2 *)(smem + prm.off_dh);      // [3][144] fp32 dH of the current slot
+    float *sV = (float *)(smem + prm.off_b);          // drained accumulators (overlays B and A)
+    uint64_t *bar_mma = (uint64_t *)(smem + prm.off_bar);
+    uint64_t *bar_g = bar_mma + 2;
+    uint64_t *bar_job = bar_mma + 4;
+    uint64_t *bar_fin = bar_mma + 5;                 // only for draining MMAs on abort
+    uint32_t *s_tmem = (uint32_t *)(bar_mma + 6);
+    int *s_abort = (int *)(s_tmem + 1);
+    int *s_nvalid = s_abort + 1;
+    int *s_slot = s_nvalid + 1;                       // [kMaxSlots] valid slot indices
+    int *s_f = s_slot + kMaxSlots;                    // [kMaxSlots] their neighbour atoms
+
+    if (tid == 0) {
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        mbar_init(&bar_g[0], 1);
+        mbar_init(&bar_g[1], 1);
+        mbar_init(bar_job, 1);
+        mbar_init(bar_fin, 1);
+        fence_mbar_init();
+        *s_abort = 0;
+        int nv = 0;
+        for (int b = 0; b < d.nb && nv < kMaxSlots; ++b) {
+            const int f = __ldg(prm.neigh + (size_t)a * d.nb + b);
+            if (f >= 0) {
+                s_slot[nv] = b;
+                s_f[nv] = f;
+                ++nv;
+            }
+        }
+        *s_nvalid = nv;
+    }
+    if (warp == 0) {
+        tmem_alloc(s_tmem, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    const int nvalid = *s_nvalid;
+    const int njobs = (t_end - t_begin) * nvalid;
+    const int total = njobs * prm.nst;
+
+    if (nvalid == 0) {
+        // no neighbours: Sigma is zero on this CTA's points
+        for (int t = t_begin; t < t_end; ++t)
+            for (int x = tid; x < NK * GG::TE * kCh; x += kThreads) {
+                const int e = x / (NK * kCh), k = (x / kCh) % NK, c = x % kCh;
+                const int E = t * GG::TE + e;
+                if (E < d.ne) {
+                    CT z;
+                    z.x = 0;
+                    z.y = 0;
+                    S[(((size_t)k * d.ne + E) * d.na + a) * kCh + c] = z;
+                }
+            }
+    }
+
+    // Decode a global stage index into (tile, valid-slot index, stage within the job).
+    auto decode = [&](int g, int &t, int &vs, int &st) {
+        const int job = g / prm.nst;
+        st = g - job * prm.nst;
+        t = t_begin + job / nvalid;
+        vs = job % nvalid;
+    };
+    // Thread 0: bulk-copy the G blocks of stage g into raw buffer g % 2.
+    auto issue_g = [&](int g) {
+        int t, vs, st;
+        decode(g, t, vs, st);
+        const int f = s_f[vs];
+        const int e_first = t * GG::TE - omega_max + GG::P * st;
+        uint32_t bytes = 0;
+#pragma unroll
+        for (int p = 0; p < GG::P; ++p) {
+            const int Ep = e_first + p;
+            if (Ep >= 0 && Ep < d.ne) bytes += NK * kCh * (uint32_t)sizeof(CT);
+        }
+        uint64_t *bar = &bar_g[g & 1];
+        mbar_arrive_expect_tx(bar, bytes);
+        uint8_t *dst = sG + (g & 1) * prm.g_stage;
+#pragma unroll
+        for (int p = 0; p < GG::P; ++p) {
+            const int Ep = e_first + p;
+            if (Ep < 0 || Ep >= d.ne) continue;
+            for (int kp = 0; kp < NK; ++kp)
+                bulk_g2s(dst + (p * NK + kp) * kCh * sizeof(CT),
+                         G + (((size_t)kp * d.ne + Ep) * d.na + f) * kCh, kCh * (uint32_t)sizeof(CT), bar);
+        }
+    };
+
+    // Per-thread A-builder row: thread -> (accumulator q, row m).
+    const int aq = tid >> 7, am = tid & 127;
+    const bool arow_ok = am < GG::ROWS;
+    const int ae = am / (3 * NK), ak = (am / 3) % NK, aj = am % 3;
+
+    if (tid == 0 && total > 0) issue_g(0);
+
+    bool abort = false;
+    int abort_g = -1;
+    for (int g = 0; g < total && !abort; ++g) {
+        int t, vs, st;
+        decode(g, t, vs, st);
+        const int sb = g & 1;
+        const int E0 = t * GG::TE;
+        const int job = g / prm.nst;
+        const bool job_first = st == 0, job_last = st == prm.nst - 1;
+
+        if (job_first) {
+            // Slot tables for this job: dH (fp32) and the folded, split, k-rotated Dt.
+            // The previous job's MMAs are complete, so the A/B area is free scratch.
+            const int b = s_slot[vs];
+            const CT *dh = dH + ((size_t)a * d.nb + b) * 3 * kCh;
+            for (int x = tid; x < 3 * kCh; x += kThreads) sDh[x] = load_c32(dh + x);
+            uint32_t *tmp = (uint32_t *)sB;  // [kappa][w][ij][re, im]
+            for (int x = tid; x < NK * nw * 9; x += kThreads) {
+                const int ij = x % 9, w = (x / 9) % nw, kap = x / (9 * nw);
+                // fold qz onto kz' = qz mod Nkz: T depends on (k - k') mod Nkz only
+                float2 acc = make_float2(0.f, 0.f);
+                for (int q = kap; q < d.nqz; q += NK) {
+                    const float2 v = load_c32(D + ((((size_t)q * nw + w) * d.na + a) * d.nb + b) * 9 + ij);
+                    acc.x += v.x;
+                    acc.y += v.y;
+                }
+                tmp[2 * x] = split_bf16(acc.x);
+                tmp[2 * x + 1] = split_bf16(acc.y);
+            }
+            __syncthreads();
+            for (int x = tid; x < NK * NK * nw * 9; x += kThreads) {
+                const int ij = x % 9, w = (x / 9) % nw, kp = (x / (9 * nw)) % NK, k = x / (9 * nw * NK);
+                const int kap = (k - kp + NK) % NK;
+                const int src = (kap * nw + w) * 9 + ij;
+                sDf[2 * x] = tmp[2 * src];
+                sDf[2 * x + 1] = tmp[2 * src + 1];
+            }
+            __syncthreads();
+        }
+
+        // another CTA timed out: stop early instead of waiting out every bound
+        if (tid == 0 && *(volatile int32_t *)prm.status != 0) *s_abort = 1;
+        if (tid == 0 && g + 1 < total) issue_g(g + 1);
+
+        // ---- G blocks of this stage: wait, convert to fp32 in place, zero the gaps ----
+        if (!mbar_wait_bounded(&bar_g[sb], (g >> 1) & 1, kWaitNs)) {
+            *s_abort = 1;
+            atomicExch(prm.status, 1);
+        }
+        uint8_t *gbuf = sG + sb * prm.g_stage;
+        float2 *g32 = (float2 *)gbuf;  // [p][k'][u][t] complex fp32
+        {
+            constexpr int NE_ = GG::P * NK * kCh;
+            constexpr int PER = (NE_ + kThreads - 1) / kThreads;
+            float2 v[PER];
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int x = tid + r * kThreads;
+                v[r] = make_float2(0.f, 0.f);
+                if (x < NE_) {
+                    const int p = x / (NK * kCh);
+                    const int Ep = E0 - omega_max + GG::P * st + p;
+                    if (Ep >= 0 && Ep < d.ne) {
+                        if (sizeof(CT) == 16) {
+                            const double2 raw = ((const double2 *)gbuf)[x];
+                            v[r] = make_float2(f64_to_f32(raw.x), f64_to_f32(raw.y));
+                        } else {
+                            v[r] = ((const float2 *)gbuf)[x];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int x = tid + r * kThreads;
+                if (x < NE_) g32[x] = v[r];
+            }
+        }
+
+        // ---- the stage buffers must be free: MMAs of stage g - 2 complete ----
+        if (g >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((g >> 1) - 1) & 1, kWaitNs)) {
+            *s_abort = 1;
+            atomicExch(prm.status, 1);
+        }
+        __syncthreads();
+
+        uint8_t *bhi = sB + sb * (2 * GG::B_PLANE), *blo = bhi + GG::B_PLANE;
+        uint8_t *abase = sA + sb * (4 * GG::A_PLANE);
+
+        // ---- X slices: X_i[k'][r, t] = sum_u dH_i[r, u] G[k'][u, t] -> B (bf16 hi / lo) ----
+        for (int item = tid; item < GG::P * kCh; item += kThreads) {
+            const int p = item / kCh, n = item % kCh, r = n / 12, tt = n % 12;
+            uint32_t hw[GG::KS / 2], lw[GG::KS / 2];
+#pragma unroll
+            for (int x = 0; x < GG::KS / 2; ++x) {
+                hw[x] = 0u;
+                lw[x] = 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float2 hrow[12];
+#pragma unroll
+                for (int u = 0; u < 12; ++u) hrow[u] = sDh[i * kCh + r * 12 + u];
+#pragma unroll
+                for (int kp = 0; kp < NK; ++kp) {
+                    const float2 *gcol = g32 + (p * NK + kp) * kCh + tt;
+                    float xr = 0.f, xi = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 12; ++u) {
+                        const float2 gv = gcol[u * 12];
+                        xr = fmaf(hrow[u].x, gv.x, xr);
+                        xr = fmaf(-hrow[u].y, gv.y, xr);
+                        xi = fmaf(hrow[u].x, gv.y, xi);
+                        xi = fmaf(hrow[u].y, gv.x, xi);
+                    }
+                    const uint32_t sr = split_bf16(xr), si = split_bf16(xi);
+                    const int pair = i * NK + kp;  // K index 2 * pair (re), 2 * pair + 1 (im)
+                    hw[pair] = __byte_perm(sr, si, 0x5410);
+                    lw[pair] = __byte_perm(sr, si, 0x7632);
+                }
+            }
+            const uint32_t row_off = (n >> 3) * GG::SBO_B + (n & 7) * 16 + (p * GG::KS / 8) * 128;
+#pragma unroll
+            for (int gq = 0; gq < GG::KS / 8; ++gq) {
+                *(uint4 *)(bhi + row_off + gq * 128) = make_uint4(hw[4 * gq], hw[4 * gq + 1], hw[4 * gq + 2], hw[4 * gq + 3]);
+                *(uint4 *)(blo + row_off + gq * 128) = make_uint4(lw[4 * gq], lw[4 * gq + 1], lw[4 * gq + 2], lw[4 * gq + 3]);
+            }
+        }
+
+        // ---- Toeplitz slice: A_q[(e, k, j), (p, i, k', re/im)] ----
+        {
+            uint8_t *ahi = abase + aq * (2 * GG::A_PLANE), *alo = ahi + GG::A_PLANE;
+            const uint32_t row_off = (am >> 3) * GG::SBO_A + (am & 7) * 16;
+            const int wrow = ae + nw - 1 - GG::P * st;  // w for p = 0
+            const uint32_t *dfrow = sDf + ((size_t)ak * NK * nw * 9 + aj) * 2;
+#pragma unroll
+            for (int gq = 0; gq < GG::KST / 8; ++gq) {
+                uint32_t wv[8];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const int kk = gq * 8 + x;
+                    const int p = kk / GG::KS, r2 = kk % GG::KS;
+                    uint32_t val = 0u;
+                    if (r2 < 6 * NK && arow_ok) {
+                        const int pair = r2 >> 1, pc = r2 & 1;
+                        const int i = pair / NK, kp = pair % NK;
+                        const int w = wrow - p;
+                        if (w >= 0 && w < nw) {
+                            const int use_im = aq ^ pc;
+                            val = dfrow[(((size_t)kp * nw + w) * 9 + i * 3) * 2 + use_im];
+                            if (aq == 0 && pc == 1) val ^= 0x80008000u;
+                        }
+                    }
+                    wv[x] = val;
+                }
+                const uint4 h4 = make_uint4(__byte_perm(wv[0], wv[1], 0x5410), __byte_perm(wv[2], wv[3], 0x5410),
+                                            __byte_perm(wv[4], wv[5], 0x5410), __byte_perm(wv[6], wv[7], 0x5410));
+                const uint4 l4 = make_uint4(__byte_perm(wv[0], wv[1], 0x7632), __byte_perm(wv[2], wv[3], 0x7632),
+                                            __byte_perm(wv[4], wv[5], 0x7632), __byte_perm(wv[6], wv[7], 0x7632));
+                *(uint4 *)(ahi + row_off + gq * 128) = h4;
+                *(uint4 *)(alo + row_off + gq * 128) = l4;
+            }
+        }
+
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (*s_abort) {
+            abort = true;
+            abort_g = g;
+            break;
+        }
+
+        // ---- MMAs of this stage (one thread) ----
+        if (tid == 0) {
+            tc_fence_after();
+            constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
+            const uint32_t bh0 = smem_u32(bhi), bl0 = smem_u32(blo);
+#pragma unroll
+            for (int ks = 0; ks < GG::KST / 16; ++ks) {
+                const uint64_t bdh = smem_desc(bh0 + ks * 256, 128, GG::SBO_B);
+                const uint64_t bdl = smem_desc(bl0 + ks * 256, 128, GG::SBO_B);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint32_t ah = smem_u32(abase + q * (2 * GG::A_PLANE)) + ks * 256;
+                    const uint64_t adh = smem_desc(ah, 128, GG::SBO_A);
+                    const uint64_t adl = smem_desc(ah + GG::A_PLANE, 128, GG::SBO_A);
+                    const uint32_t dt = tmem + (q ? kAccIm : 0u);
+                    mma_ss(dt, adh, bdh, idesc, (job_first && ks == 0) ? 0u : 1u);
+                    mma_ss(dt, adh, bdl, idesc, 1u);
+                    mma_ss(dt, adl, bdh, idesc, 1u);
+                }
+            }
+            mma_commit(&bar_mma[sb]);
+            if (job_last) mma_commit(bar_job);
+        }
+
+        if (!job_last) continue;
+
+        // ---- epilogue of the job: V = acc_re + i acc_im, Sigma += sum_j V_j dH_j^+ ----
+        if (!mbar_wait_bounded(bar_job, job & 1, kWaitNs)) {
+            *s_abort = 1;
+            atomicExch(prm.status, 1);
+        }
+        tc_fence_after();
+        const bool first_slot = vs == 0;
+        for (int h = 0; h < 2; ++h) {
+            {
+                const int qd = warp & 3, q = warp >> 2;
+                const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (q ? kAccIm : 0u) + 72 * h;
+                float *vrow = sV + (q * kRowsMax + qd * 32 + lane) * kVStride;
+#pragma unroll
+                for (int c0 = 0; c0 < 72; c0 += 8) {
+                    float v[8];
+                    tmem_ld8(taddr + c0, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) vrow[c0 + x] = v[x];
+                }
+            }
+            __syncthreads();
+            if (tid < NK * GG::TE * 6) {
+                const int pt = tid / 6, rb = (tid % 6) >> 1, sbk = tid & 1;
+                const int e = pt / NK, k = pt % NK;
+                float2 acc[2][6];
+#pragma unroll
+                for (int rl = 0; rl < 2; ++rl)
+#pragma unroll
+                    for (int s = 0; s < 6; ++s) acc[rl][s] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int m = pt * 3 + j;
+                    const float *vre = sV + m * kVStride, *vim = sV + (kRowsMax + m) * kVStride;
+#pragma unroll
+                    for (int tt = 0; tt < 12; ++tt) {
+                        float2 vv[2];
+#pragma unroll
+                        for (int rl = 0; rl < 2; ++rl) {
+                            const int col = (2 * rb + rl) * 12 + tt;
+                            vv[rl] = make_float2(vre[col], vim[col]);
+                        }
+#pragma unroll
+                        for (int s = 0; s < 6; ++s) {
+                            const float2 hv = sDh[j * kCh + (6 * sbk + s) * 12 + tt];
+#pragma unroll
+                            for (int rl = 0; rl < 2; ++rl) acc[rl][s] = cmul_conj_acc(acc[rl][s], vv[rl], hv);
+                        }
+                    }
+                }
+                const int E = E0 + e;
+                if (E < d.ne) {
+#pragma unroll
+                    for (int rl = 0; rl < 2; ++rl) {
+                        const int r = 6 * h + 2 * rb + rl;
+                        CT *dst = S + (((size_t)k * d.ne + E) * d.na + a) * kCh + r * 12 + 6 * sbk;
+#pragma unroll
+                        for (int s = 0; s < 6; ++s) rmw_store<CT>(dst + s, acc[rl][s], first_slot);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (*s_abort) {
+            abort = true;
+            abort_g = g;
+            break;
+        }
+    }
+
+    // ---- teardown: nothing of ours may still be in flight when the CTA exits ----
+    if (abort) {
+        if (tid == 0) mma_commit(bar_fin);  // arrives once every MMA issued so far is done
+        mbar_wait_bounded(bar_fin, 0, kWaitNs);
+        // the bulk copies of the aborted stage and of the one prefetched after it
+        if (abort_g >= 0) mbar_wait_bounded(&bar_g[abort_g & 1], (abort_g >> 1) & 1, kWaitNs);
+        if (abort_g + 1 < total) mbar_wait_bounded(&bar_g[(abort_g + 1) & 1], ((abort_g + 1) >> 1) & 1, kWaitNs);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int NK>
+uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
+    using GG = Geo<NK>;
+    uint32_t off = 0;
+    auto take = [&](uint32_t bytes, uint32_t align) {
+        off = (off + align - 1) / align * align;
+        const uint32_t at = off;
+        off += bytes;
+        return at;
+    };
+    // B and A stage buffers are contiguous; the drained accumulators and the unrotated
+    // Dt table of a job overlay them (never while MMAs read them)
+    const uint32_t need_v = 2 * kRowsMax * kVStride * 4;
+    const uint32_t ab = 2 * 2 * GG::B_PLANE + 2 * 4 * GG::A_PLANE;
+    prm.off_b = take(ab > need_v ? ab : need_v, 1024);
+    prm.off_a = prm.off_b + 2 * 2 * GG::B_PLANE;
+    prm.g_stage = (uint32_t)(GG::P * NK * kCh * cbytes);
+    prm.off_g = take(2 * prm.g_stage, 128);
+    const uint32_t dfr = (uint32_t)(NK * NK * d.nw * 9 * 8);
+    const uint32_t dtmp = (uint32_t)(NK * d.nw * 9 * 8);
+    prm.off_df = take(dfr, 16);
+    prm.off_dh = take(3 * kCh * 8, 16);
+    prm.off_bar = take(6 * 8 + 4 + 4 + 4 + 2 * kMaxSlots * 4, 8);
+    if (dtmp > (ab > need_v ? ab : need_v)) return 0xFFFFFFFFu;
+    return off;
+}
+
+template <int NK, typename CT>
+sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
+    using GG = Geo<NK>;
+    MixParams prm{};
+    const Dims &d = p.d;
+    const uint32_t smem = mixed_smem_bytes<NK>(d, sizeof(CT), prm);
+    if (smem > 232448u) {
+        set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
+        return SSE_E_INVALID_ARG;
+    }
+    if (((uintptr_t)io.G_gt | (uintptr_t)io.G_lt) & 15u) {
+        set_error("mixed mode: G buffers must be 16-byte aligned");
+        return SSE_E_INVALID_ARG;
+    }
+    prm.neigh = p.geo.neigh;
+    prm.dH = p.geo.dH;
+    prm.status = p.d_status;
+    prm.d = d;
+    prm.ntiles = (d.ne + GG::TE - 1) / GG::TE;
+    prm.nst = (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
+    const bool do_gt = io.S_gt != nullptr, do_lt = io.S_lt != nullptr;
+    const int nsign = (int)do_gt + (int)do_lt;
+    if (nsign == 0) return SSE_OK;
+    prm.G[0] = do_gt ? io.G_gt : io.G_lt;
+    prm.D[0] = do_gt ? io.D_gt : io.D_lt;
+    prm.S[0] = do_gt ? io.S_gt : io.S_lt;
+    prm.G[1] = io.G_lt;
+    prm.D[1] = io.D_lt;
+    prm.S[1] = io.S_lt;
+    // tiles per CTA: enough CTAs for several waves over the SMs, at least 1 tile each
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+    const long long units = (long long)nsign * d.na;
+    int tpc = prm.ntiles;
+    while (tpc > 1 && units * ((prm.ntiles + tpc - 1) / tpc) < 8LL * sms) tpc = (tpc + 1) / 2;
+    prm.tiles_per_cta = tpc;
+    prm.nchunks = (prm.ntiles + tpc - 1) / tpc;
+    const long long gx = (long long)d.na * prm.nchunks;
+    if (gx > 0x7fffffffLL) {
+        set_error("mixed mode: grid too large");
+        return SSE_E_INVALID_ARG;
+    }
+    auto kern = sse_mixed_kernel<NK, CT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed kernel)");
+    kern<<<dim3((unsigned)gx, nsign), kThreads, smem, st>>>(prm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch sse_mixed_kernel");
+    p.tile_e = GG::TE;
+    return SSE_OK;
+}
+
+template <typename CT>
+sse_status launch_dtype(Plan &p, const sse_io &io, cudaStream_t st) {
+    switch (p.d.nkz) {
+        case 1: return launch_nk<1, CT>(p, io, st);
+        case 2: return launch_nk<2, CT>(p, io, st);
+        case 3: return launch_nk<3, CT>(p, io, st);
+        case 4: return launch_nk<4, CT>(p, io, st);
+        case 5: return launch_nk<5, CT>(p, io, st);
+        default:
+            set_error("mixed mode supports Nkz <= 5 (got %d)", p.d.nkz);
+            return SSE_E_INVALID_ARG;
+    }
+}
+
+template <int NK>
+int tile_e_of() {
+    return Geo<NK>::TE;
+}
+
+}  // namespace
+
 sse_status mixed_plan_init(Plan &p) {
-    (void)p;
-    set_error("mixed mode is not built into this library yet");
-    return SSE_E_INVALID_ARG;
+    const Dims &d = p.d;
+    if (d.nkz < 1 || d.nkz > 5) {
+        set_error("mixed mode supports Nkz <= 5 (got %d)", d.nkz);
+        return SSE_E_INVALID_ARG;
+    }
+    if (d.nb > kMaxSlots) {
+        set_error("mixed mode supports nb_max <= %d (got %d)", kMaxSlots, d.nb);
+        return SSE_E_INVALID_ARG;
+    }
+    MixParams prm{};
+    uint32_t smem = 0;
+    const size_t cb = elem_bytes(p.geo.dtype);
+    switch (d.nkz) {
+        case 1: smem = mixed_smem_bytes<1>(d, cb, prm); p.tile_e = tile_e_of<1>(); break;
+        case 2: smem = mixed_smem_bytes<2>(d, cb, prm); p.tile_e = tile_e_of<2>(); break;
+        case 3: smem = mixed_smem_bytes<3>(d, cb, prm); p.tile_e = tile_e_of<3>(); break;
+        case 4: smem = mixed_smem_bytes<4>(d, cb, prm); p.tile_e = tile_e_of<4>(); break;
+        default: smem = mixed_smem_bytes<5>(d, cb, prm); p.tile_e = tile_e_of<5>(); break;
+    }
+    if (smem > 232448u) {
+        set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
+        return SSE_E_INVALID_ARG;
+    }
+    return SSE_OK;
 }
+
 void mixed_plan_free(Plan &p) { (void)p; }
+
 sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st) {
-    (void)p; (void)io; (void)st;
-    set_error("mixed mode is not built into this library yet");
-    return SSE_E_INVALID_ARG;
+    if (p.geo.dtype == SSE_C128) return launch_dtype<double2>(p, io, st);
+    return launch_dtype<float2>(p, io, st);
 }
+
 }  // namespace sse

@@ -1,0 +1,131 @@
+"""Mixed-precision tensor-core kernel vs the CPU FP64 oracle, through the C ABI.
+
+Tolerance: relative Frobenius error <= 2e-5 per sign (the mixed path's stated bound).
+Cases span several tiles with a ragged last tile, every supported Nkz, qz wrap with
+Nqz != Nkz, omega offsets, energies below the grid, empty / duplicate / self slots,
+complex64 storage, and the full medium and precision workloads on sampled outputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_08810_gb300 import inputs
+from tests.gpu_helpers import max_block_rel, rel_fro, run
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-5
+
+
+def oracle_full(inst, sign, omega_first=1):
+    return oracle.sigma_atoms(inst["G_" + sign], inst["D_" + sign], inst["dH"], inst["neigh"],
+                              omega_first=omega_first)
+
+
+def test_tiny_config_both_signs():
+    inst = inputs.make_instance(inputs.TINY, 0)
+    out = run(inst, "mixed")
+    for s in ("gt", "lt"):
+        ref = oracle_full(inst, s)
+        assert rel_fro(out[s], ref) <= TOL
+        assert max_block_rel(out[s], ref) <= 1e-3
+        # the anti-Hermiticity invariant survives the mixed arithmetic to its precision
+        assert rel_fro(out[s], -np.conj(np.swapaxes(out[s], -1, -2))) <= 2 * TOL
+
+
+@pytest.mark.parametrize("nkz", [1, 2, 3, 4, 5])
+def test_every_supported_nkz(nkz):
+    # NE = 3 tiles + a ragged tail for every tile height
+    geo = inputs.Geometry(nkz=nkz, nqz=nkz, ne=3 * (128 // (3 * nkz)) + 5, nw=6, na=6, nb=4)
+    inst = inputs.make_instance(geo, 30 + nkz)
+    out = run(inst, "mixed")
+    for s in ("gt", "lt"):
+        assert rel_fro(out[s], oracle_full(inst, s)) <= TOL
+
+
+@pytest.mark.parametrize("case", [
+    dict(nkz=3, nqz=5, ne=40, nw=5, na=7, nb=3, omega_first=1),   # qz folds onto kz
+    dict(nkz=4, nqz=2, ne=23, nw=6, na=5, nb=2, omega_first=0),   # omega_first = 0
+    dict(nkz=2, nqz=2, ne=5, nw=9, na=6, nb=2, omega_first=2),    # most E - omega below the grid
+    dict(nkz=1, nqz=1, ne=70, nw=16, na=1, nb=4, omega_first=1),  # one atom, self slots
+    dict(nkz=5, nqz=5, ne=17, nw=32, na=3, nb=4, omega_first=1),  # Nw = 32 with a short grid
+])
+def test_edge_geometries(case):
+    of = case.pop("omega_first")
+    geo = inputs.Geometry(norb=12, omega_first=of, **case)
+    rng = np.random.default_rng(9)
+    neigh = rng.integers(0, geo.na, size=(geo.na, geo.nb)).astype(np.int32)
+    inst = inputs.make_instance(geo, 41, neigh=neigh, hermitian_pairs=False)
+    out = run(inst, "mixed", omega_first=of)
+    for s in ("gt", "lt"):
+        assert rel_fro(out[s], oracle_full(inst, s, of)) <= TOL
+
+
+def test_empty_duplicate_slots_single_sign_and_isolated_atom():
+    geo = inputs.Geometry(nkz=3, nqz=3, ne=30, nw=4, na=9, nb=5)
+    neigh = inputs.chain_neighbours(9, (-2, -1, 1, 2, 1))
+    neigh[3, 1] = -1
+    neigh[7, :] = -1
+    inst = inputs.make_instance(geo, 23, neigh=neigh, hermitian_pairs=False)
+    out = run(inst, "mixed", signs=("gt",))
+    assert rel_fro(out["gt"], oracle_full(inst, "gt")) <= TOL
+    assert np.all(out["gt"][:, :, 7] == 0)
+
+
+def test_complex64_batched_shape():
+    """One instance shaped like the batched workload: Nkz=Nqz=3, Nw=16, per-atom
+    neighbour counts 3..8 within +-8 sites, complex64 storage."""
+    rng = np.random.default_rng(3)
+    na, ne = 150, 77
+    neigh = inputs.random_neighbours(rng, na, nb_max=8)
+    geo = inputs.Geometry(nkz=3, nqz=3, ne=ne, nw=16, na=na, nb=8)
+    inst = inputs.make_instance(geo, 5, dtype=np.complex64, neigh=neigh, hermitian_pairs=False)
+    out = run(inst, "mixed")
+    for s in ("gt", "lt"):
+        assert rel_fro(out[s], oracle_full(inst, s)) <= TOL
+
+
+def test_mixed_matches_fp64_kernel_on_tiny():
+    inst = inputs.make_instance(inputs.TINY, 7)
+    a = run(inst, "mixed")
+    b = run(inst, "fp64")
+    for s in ("gt", "lt"):
+        assert rel_fro(a[s], b[s]) <= TOL
+
+
+def sampled_points(geo, n, seed):
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0, 0), (geo.nkz - 1, geo.ne - 1, geo.na - 1), (1, 1, 3), (2, geo.nw, 100 % geo.na),
+           (geo.nkz - 1, geo.nw + 1, geo.na // 2)]
+    pts += [tuple(int(x) for x in (rng.integers(geo.nkz), rng.integers(geo.ne), rng.integers(geo.na)))
+            for _ in range(n)]
+    return pts
+
+
+def test_medium_config_sampled_points():
+    """Full medium workload (the benchmark's launch), checked on sampled output blocks
+    that the oracle evaluates one by one; plus whole-tensor invariants."""
+    geo = inputs.MEDIUM
+    inst = inputs.make_instance(geo, 1)
+    out = run(inst, "mixed")
+    pts = sampled_points(geo, 12, 0)
+    for s in ("gt", "lt"):
+        ref = oracle.sigma_points(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], pts)
+        got = np.stack([out[s][k, e, a] for k, e, a in pts])
+        assert rel_fro(got, ref) <= TOL
+        assert np.all(out[s][:, 0] == 0)
+        assert np.all(np.isfinite(out[s]))
+        assert rel_fro(out[s], -np.conj(np.swapaxes(out[s], -1, -2))) <= 2 * TOL
+
+
+def test_precision_config_atom_slice():
+    """Precision workload (Na = 2048, G about 6 GB per sign in complex128, seed 2):
+    the error is measured against the oracle on a slice of atoms plus sampled points."""
+    geo = inputs.PRECISION
+    inst = inputs.make_instance(geo, 2)
+    out = run(inst, "mixed", signs=("gt",))
+    ref = oracle.sigma_atoms(inst["G_gt"], inst["D_gt"], inst["dH"], inst["neigh"], 0, 8)
+    assert rel_fro(out["gt"][:, :, 0:8], ref) <= TOL
+    pts = sampled_points(geo, 8, 1)
+    refp = oracle.sigma_points(inst["G_gt"], inst["D_gt"], inst["dH"], inst["neigh"], pts)
+    got = np.stack([out["gt"][k, e, a] for k, e, a in pts])
+    assert rel_fro(got, refp) <= TOL
