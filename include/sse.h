@@ -124,6 +124,22 @@ SSE_API sse_status sse_execute_host(sse_plan_t *plan, const sse_io *host_io, voi
  * its kernels write: SSE_OK, or SSE_E_TIMEOUT if a bounded device wait expired. */
 SSE_API sse_status sse_plan_status(sse_plan_t *plan);
 
+/* Mixed-mode evaluation for callers that cannot let this library allocate memory (for
+ * example a framework whose allocator owns all device memory, or a loop that must not
+ * stall on cudaMalloc/cudaFree).  No plan is created and nothing is allocated: the
+ * neighbour list is range-checked on the device, and the little scratch the kernels
+ * need (4 words: the check's result and the kernel's device-wait status) lives in one
+ * fixed 256-byte device array built into the library, which every GPU that loads the
+ * library keeps until the process exits.  The paper has no counterpart to this entry.
+ * The first call on a device looks up that array's address; make it before any stream
+ * capture.  All calls on a device share the array (each clears what it uses first), so
+ * calls whose work overlaps on the GPU race.  Same arguments and results as sse_plan +
+ * sse_execute in SSE_MODE_MIXED; geometries the mixed kernel cannot run (Nkz > 5,
+ * nb_max > 32, or a shared-memory need beyond one SM) are rejected with
+ * SSE_E_INVALID_ARG.  Synchronous: returns after Sigma is written (it synchronises
+ * `stream`); SSE_E_TIMEOUT if a bounded device wait expired. */
+SSE_API sse_status sse_execute_noalloc(const sse_geometry *geo, const sse_io *io, void *stream);
+
 SSE_API const char *sse_status_string(sse_status status);
 SSE_API const char *sse_last_error(void);
 SSE_API int32_t sse_abi_version(void);

@@ -37,6 +37,7 @@ SSE_MODE_MIXED = 1
 EXPORTED = (
     "sse_plan", "sse_plan_destroy", "sse_plan_query", "sse_execute", "sse_execute_host",
     "sse_plan_status", "sse_status_string", "sse_last_error", "sse_abi_version",
+    "sse_execute_noalloc",
 )
 
 
@@ -92,6 +93,7 @@ def load(path: Optional[str] = None):
             "sse_status_string": ([st], ctypes.c_char_p),
             "sse_last_error": ([], ctypes.c_char_p),
             "sse_abi_version": ([], st),
+            "sse_execute_noalloc": ([ctypes.POINTER(sse_geometry), ctypes.POINTER(sse_io), vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -143,6 +145,12 @@ def sse_execute_host(plan, io: sse_io, stream: int = 0) -> None:
 
 def sse_plan_status(plan) -> None:
     _check(load().sse_plan_status(plan), "sse_plan_status")
+
+
+def sse_execute_noalloc(geo: sse_geometry, io: sse_io, stream: int = 0) -> None:
+    """Mixed-mode evaluation that allocates nothing (see include/sse.h); synchronous."""
+    _check(load().sse_execute_noalloc(ctypes.byref(geo), ctypes.byref(io), ctypes.c_void_p(stream)),
+           "sse_execute_noalloc")
 
 
 def sse_status_string(status: int) -> str:
