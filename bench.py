@@ -45,17 +45,24 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", choices=("auto", "mixed", "fp64"), default="auto")
-    ap.add_argument("--workload", choices=("medium", "tiny"), default="medium")
+    ap.add_argument("--workload", choices=("medium", "medium64", "tiny"), default="medium",
+                    help="medium: the benchmark workload; medium64: the same shape with Na=64 "
+                         "(small case for profiling); tiny: the smallest workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="timed steps of the plain FP64 form measured beside the mixed form")
+    ap.add_argument("--batched", action="store_true",
+                    help="also time the batched workload (64 uneven instances, one persistent launch)")
+    ap.add_argument("--serving", type=int, default=0, metavar="N",
+                    help="also run the serving workload with N Poisson-arriving requests (0: off)")
     return ap.parse_args()
 
 
 def workload(name):
     from paper_1912_08810_gb300 import inputs
-    return {"medium": (inputs.MEDIUM, 1), "tiny": (inputs.TINY, 0)}[name]
+    small = inputs.Geometry(nkz=5, nqz=5, ne=256, nw=32, na=64, nb=4)
+    return {"medium": (inputs.MEDIUM, 1), "medium64": (small, 1), "tiny": (inputs.TINY, 0)}[name]
 
 
 def config_dict(geo, name, form):
@@ -248,6 +255,7 @@ def run_ours(args):
             form = "fp64"
     if plan is None:
         plan = make_plan("fp64")
+    plan_keep = [plan]
     info = plan.info()
     points = geo.points()
     flops_step = 2 * info.flops_per_sign
@@ -313,6 +321,7 @@ def run_ours(args):
                             "roofline_frac": a64 / FP64_NOMINAL_TFLOPS, "speedup_of_value": value / v64}
         p64.close()
 
+    hostin, hostout = {}, {}
     if not args.no_e2e:
         hostin = {k: torch.from_numpy(inst[k]).pin_memory() for k in ("G_gt", "G_lt", "D_gt", "D_lt")}
         hostout = {s: torch.empty(S[s].shape, dtype=S[s].dtype).pin_memory() for s in ("gt", "lt")}
@@ -337,12 +346,178 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_sample(inst, geo)
+    del hostin, hostout
+    if args.batched or args.serving:
+        del dev, S, plan_keep[:]
+        torch.cuda.empty_cache()
+    if args.batched:
+        out["batched"] = run_batched(args, stream, peaks)
+        out["gpu_launches"] += out["batched"]["gpu_launches"]
+    if args.serving:
+        out["serving"] = run_serving(args.serving)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    plan.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batched(args, stream, peaks):
+    """The batched workload: 64 instances (Na ~ U[64,1024], NE ~ U[64,512], Nkz=Nqz=3,
+    Nw=16, 3..8 random neighbours within +-8 sites, complex64, seed 3), drawn on the device,
+    evaluated by one persistent launch per step; the step is captured in a CUDA graph and
+    replayed.  The first call runs the autotuner."""
+    import torch
+
+    from paper_1912_08810_gb300 import inputs, sse
+    spec = inputs.BatchedSpec()
+    insts = inputs.make_batched_torch(spec, 3)
+    plans, ios, outs = [], [], []
+    points = 0
+    flops = 0.0
+    for inst in insts:
+        g = inst["geometry"]
+        S = {s: torch.empty_like(inst["G_gt"]) for s in ("gt", "lt")}
+        p = sse.Plan(inst["neigh"], inst["dH"], nkz=g.nkz, nqz=g.nqz, ne=g.ne, nw=g.nw, mode="mixed")
+        ios.append(p._io(inst["G_gt"], inst["G_lt"], inst["D_gt"], inst["D_lt"], S["gt"], S["lt"]))
+        plans.append(p)
+        outs.append(S)
+        points += g.points()
+        flops += 2 * p.info().flops_per_sign
+    handles = [p.handle for p in plans]
+    side = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(side):
+        sse.sse_execute_batch(handles, ios, side.cuda_stream)  # first call: autotune
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    tuning = sse.sse_batch_tuning(handles, ios)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        sse.sse_execute_batch(handles, ios, side.cuda_stream)
+    steps, warm = max(2, min(args.steps, 3)), 1
+    for _ in range(warm):
+        graph.replay()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    cur = torch.cuda.current_stream()
+    for a, b in evs:
+        a.record(cur)
+        graph.replay()
+        b.record(cur)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in evs]
+    plans[0].status()
+    ms = statistics.mean(per)
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    achieved = flops / (ms / 1e3) / 1e12
+    res = {"workload": "64 instances, Na~U[64,1024], NE~U[64,512], Nkz=Nqz=3, Nw=16, Nb~U{3..8} "
+                       "within +-8 sites, complex64, seed 3 (drawn on device)",
+           "points_per_step": points, "value": points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "p50_ms": pct(per, 50), "p99_ms": pct(per, 99), "steps": steps, "warmup": warm,
+           "tiles_per_unit": tuning[0] if tuning else None, "longest_first": tuning[1] if tuning else None,
+           "autotune_s": tune_s, "graph_captured": True, "gpu_launches": steps + warm,
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16 / SPLIT_PRODUCTS,
+                        "unit": "TFLOP/s", "frac": achieved / (bf16 / SPLIT_PRODUCTS)}}
+    for p in plans:
+        p.close()
+    del insts, outs, graph
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_serving(n_requests, seed=4):
+    """Serving workload: n_requests arriving as a Poisson stream over resident sessions
+    drawn from the batched size distribution (95 %) plus large sessions (5 %: Na=2048,
+    NE=256), each session an SCBA-style repeat (one request in flight per session, its
+    buffers stay on the device), admitted against a 120 GB budget.  The arrival rate is
+    calibrated to about 80 % of the measured service rate.  Latency = completion - arrival."""
+    import numpy as np
+    import torch
+
+    from paper_1912_08810_gb300 import inputs, sse
+    rng = np.random.default_rng(seed)
+    spec = inputs.BatchedSpec(n_instances=24)
+    sessions = []
+    for inst in inputs.make_batched_torch(spec, seed):
+        sessions.append(("normal", inst))
+    big = inputs.Geometry(nkz=3, nqz=3, ne=256, nw=16, na=2048, nb=8)
+    for j in range(2):
+        nrng = np.random.default_rng([seed, 1000 + j])
+        neigh = inputs.random_neighbours(nrng, big.na, 8)
+        inst = inputs.make_instance_torch(big, 10_000 + j, neigh=neigh, hermitian_pairs=False)
+        inst["geometry"] = big
+        sessions.append(("large", inst))
+    objs = []
+    for kind, inst in sessions:
+        g = inst["geometry"]
+        S = {s: torch.empty_like(inst["G_gt"]) for s in ("gt", "lt")}
+        p = sse.Plan(inst["neigh"], inst["dH"], nkz=g.nkz, nqz=g.nqz, ne=g.ne, nw=g.nw, mode="mixed")
+        io = p._io(inst["G_gt"], inst["G_lt"], inst["D_gt"], inst["D_lt"], S["gt"], S["lt"])
+        objs.append(dict(kind=kind, plan=p, io=io, S=S, points=g.points()))
+    # calibration: each session alone, warm, with the split the server uses (no tuning)
+    service = []
+    old = os.environ.get("SSE_AUTOTUNE")
+    os.environ["SSE_AUTOTUNE"] = "0"
+    for o in objs:
+        sse.sse_execute_batch([o["plan"].handle], [o["io"]], 0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sse.sse_execute_batch([o["plan"].handle], [o["io"]], 0)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t)
+    if old is None:
+        del os.environ["SSE_AUTOTUNE"]
+    else:
+        os.environ["SSE_AUTOTUNE"] = old
+    normal = [i for i, o in enumerate(objs) if o["kind"] == "normal"]
+    large = [i for i, o in enumerate(objs) if o["kind"] == "large"]
+    mean_s = 0.95 * float(np.mean([service[i] for i in normal])) + 0.05 * float(np.mean([service[i] for i in large]))
+    rate = 0.8 / mean_s
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    which = [int(rng.choice(large)) if rng.random() < 0.05 else int(rng.choice(normal)) for _ in range(n_requests)]
+    server = sse.sse_server_create(120 << 30, 64, 30000)
+    busy = {}
+    waiting = {i: [] for i in range(len(objs))}
+    lat, done_points = [], 0
+    t0 = time.perf_counter()
+    nxt = 0
+    inflight = {}
+    try:
+        while len(lat) < n_requests:
+            now = time.perf_counter() - t0
+            while nxt < n_requests and arrivals[nxt] <= now:
+                waiting[which[nxt]].append((nxt, arrivals[nxt]))
+                nxt += 1
+            for sidx, q in waiting.items():
+                if q and sidx not in busy:
+                    rid, arr = q.pop(0)
+                    o = objs[sidx]
+                    tk = sse.sse_submit(server, o["plan"].handle, o["io"])
+                    busy[sidx] = tk
+                    inflight[tk] = (sidx, rid, arr)
+            for tk in list(inflight):
+                rc, r = sse.sse_poll(server, tk)
+                if rc == sse.SSE_NOT_READY:
+                    continue
+                if rc != sse.SSE_OK:
+                    raise RuntimeError(f"serving request failed: {sse.status_name(rc)}")
+                sidx, rid, arr = inflight.pop(tk)
+                del busy[sidx]
+                lat.append((time.perf_counter() - t0 - arr) * 1e3)
+                done_points += objs[sidx]["points"]
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        rounds, _, _ = sse.sse_server_stats(server)
+    finally:
+        sse.sse_server_destroy(server)
+    for o in objs:
+        o["plan"].close()
+    torch.cuda.empty_cache()
+    return {"requests": n_requests, "sessions": len(objs), "large_fraction": 0.05,
+            "arrival_rate_per_s": rate, "budget_gb": 120, "value": done_points / wall, "unit": UNIT,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(np.mean(lat)),
+            "rounds": rounds, "requests_per_round": n_requests / max(rounds, 1), "wall_s": wall}
 
 
 def cpu_sample(inst, geo, n_atoms=None):

@@ -120,6 +120,63 @@ SSE_API sse_status sse_execute(sse_plan_t *plan, const sse_io *io, void *stream)
  * the stream before returning.  Staging is allocated on first use and kept. */
 SSE_API sse_status sse_execute_host(sse_plan_t *plan, const sse_io *host_io, void *stream);
 
+/* Batched form (row a6): evaluate n independent instances -- each with its own plan and
+ * buffers, uneven na, ne, nb_max and nqz allowed -- in one persistent launch of the
+ * mixed kernel: one CTA per SM pulls work units (sign, atom, range of energy tiles) from
+ * a device counter until none are left.  All plans must be SSE_MODE_MIXED with equal
+ * nkz, nw, omega_first and dtype.  The split of the work (tiles per unit, and whether the
+ * longest units enter the queue first) comes from an exhaustive autotuner: the first call
+ * for a batch shape times every candidate on `stream` (synchronously, so make that call
+ * before any stream capture); later calls reuse the choice, which can be persisted in the
+ * file named by SSE_AUTOTUNE_CACHE (SSE_AUTOTUNE=0 skips tuning).  After tuning, the call
+ * is asynchronous and stream-ordered (it allocates its 4-byte work counter with
+ * cudaMallocAsync on `stream`), so it can be captured in a CUDA graph.  Results equal those
+ * of sse_execute on each instance alone, bit for bit.  Device-wait timeouts are recorded
+ * in plans[0]'s status word. */
+SSE_API sse_status sse_execute_batch(sse_plan_t *const *plans, const sse_io *ios, int32_t n, void *stream);
+
+/* The autotuner's choice for this batch shape: SSE_OK with the values, or SSE_NOT_READY
+ * if the shape has not been tuned yet. */
+SSE_API sse_status sse_batch_tuning(sse_plan_t *const *plans, const sse_io *ios, int32_t n, int32_t *tiles_per_unit,
+                                    int32_t *longest_first);
+
+/* ---- serving (row a7): a request loop with continuous batching -------------------------
+ *
+ * A server owns a host thread and two CUDA streams on the device current at creation.
+ * Requests (a mixed-mode plan plus device buffers the caller keeps resident between SCBA
+ * iterations) are admitted in arrival order while the sum of the admitted requests'
+ * resident bytes (G, Dt and Sigma of each requested sign) stays within mem_budget_bytes
+ * and at most max_inflight are admitted.  Every admitted request that has not started
+ * joins the next round: one persistent batched launch (as sse_execute_batch, with the
+ * tuned split when the shape was tuned before, else the default split), launched on the
+ * stream the previous round did not use, so new arrivals start while older rounds drain.
+ * A ticket borrows its plan and buffers until sse_poll returns a final status. */
+typedef struct {
+    sse_status status;    /* final status once sse_poll stops returning SSE_NOT_READY */
+    double t_submit_ms;   /* host steady-clock times (milliseconds) */
+    double t_start_ms;    /* when its round was launched (0 while pending) */
+    double t_end_ms;      /* when the server saw its round complete */
+    int32_t round_size;   /* requests in the round it ran in */
+} sse_result;
+
+/* wait_limit_ms bounds how long sse_server_destroy waits for running rounds (0: 1000). */
+SSE_API sse_status sse_server_create(uint64_t mem_budget_bytes, int32_t max_inflight, uint32_t wait_limit_ms,
+                                     sse_server_t **out);
+/* Non-blocking.  SSE_E_OVER_BUDGET if the request alone exceeds the budget (it could never
+ * be admitted); SSE_E_SHUTDOWN during destruction. */
+SSE_API sse_status sse_submit(sse_server_t *server, sse_plan_t *plan, const sse_io *io, uint64_t *ticket);
+/* SSE_NOT_READY while queued or running; then the request's final status (SSE_OK, a CUDA
+ * or timeout error, or SSE_E_CANCELLED), after which the ticket is forgotten and later
+ * polls give SSE_E_UNKNOWN_TICKET.  `out` (may be NULL) receives status and timestamps. */
+SSE_API sse_status sse_poll(sse_server_t *server, uint64_t ticket, sse_result *out);
+/* Cancels requests that have not started, waits up to wait_limit_ms for running rounds,
+ * then frees the server (SSE_E_TIMEOUT, and the server is not freed, if rounds are still
+ * running then). */
+SSE_API sse_status sse_server_destroy(sse_server_t *server);
+/* Rounds launched so far and the admitted working set (bytes, requests). */
+SSE_API sse_status sse_server_stats(sse_server_t *server, uint64_t *rounds, uint64_t *inflight_bytes,
+                                    int32_t *inflight);
+
 /* Synchronise the plan's last stream and read (then clear) the device status word that
  * its kernels write: SSE_OK, or SSE_E_TIMEOUT if a bounded device wait expired. */
 SSE_API sse_status sse_plan_status(sse_plan_t *plan);

@@ -90,7 +90,14 @@ using namespace sse;
 struct sse_plan_s : public Plan {
     std::vector<int32_t> neigh_host;
     double cmacs_per_sign = 0.0;
+    double slots_per_atom = 0.0;  // mean valid neighbour slots per atom
 };
+
+namespace sse {
+Plan *plan_core(sse_plan_t *p) { return p; }
+double plan_slots_per_atom(const sse_plan_t *p) { return p->slots_per_atom; }
+sse_status plan_check_io(sse_plan_t *p, const sse_io *io) { return check_io(*p, io); }
+}  // namespace sse
 
 extern "C" {
 
@@ -145,6 +152,11 @@ sse_status sse_plan(const sse_geometry *geo, sse_plan_t **out) {
         }
     }
     p->cmacs_per_sign = algorithmic_cmacs(p->d, p->neigh_host);
+    {
+        size_t valid = 0;
+        for (int32_t f : p->neigh_host) valid += f >= 0;
+        p->slots_per_atom = (double)valid / geo->na;
+    }
     e = cudaMalloc(&p->d_status, sizeof(int32_t));
     if (e != cudaSuccess) {
         delete p;
@@ -253,6 +265,49 @@ sse_status sse_execute_host(sse_plan_t *plan, const sse_io *h, void *stream) {
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "synchronise after sse_execute_host");
+    return SSE_OK;
+}
+
+// Shared checks of a batch: every plan mixed-mode with the same Nkz, Nw, omega_first, dtype.
+static sse_status check_batch(sse_plan_t *const *plans, const sse_io *ios, int32_t n) {
+    if (n < 0 || (n > 0 && (!plans || !ios))) return set_error("bad batch arguments"), SSE_E_INVALID_ARG;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!plans[i]) return set_error("plans[%d] is NULL", i), SSE_E_INVALID_ARG;
+        if (plans[i]->kernel_id != 1) return set_error("plans[%d] is not a mixed-mode plan", i), SSE_E_INVALID_ARG;
+        const Dims &a = plans[i]->d, &b = plans[0]->d;
+        if (a.nkz != b.nkz || a.nw != b.nw || a.omega_first != b.omega_first ||
+            plans[i]->geo.dtype != plans[0]->geo.dtype)
+            return set_error("plans[%d] differs from plans[0] in nkz, nw, omega_first or dtype", i), SSE_E_INVALID_ARG;
+        sse_status st = check_io(*plans[i], &ios[i]);
+        if (st != SSE_OK) return st;
+    }
+    return SSE_OK;
+}
+
+sse_status sse_execute_batch(sse_plan_t *const *plans, const sse_io *ios, int32_t n, void *stream) {
+    sse_status st = check_batch(plans, ios, n);
+    if (st != SSE_OK || n == 0) return st;
+    std::vector<Plan *> ps((size_t)n);
+    std::vector<double> slots((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        ps[i] = plans[i];
+        slots[i] = plans[i]->slots_per_atom;
+        plans[i]->last_stream = (cudaStream_t)stream;
+    }
+    return run_batch(ps.data(), slots.data(), ios, n, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+sse_status sse_batch_tuning(sse_plan_t *const *plans, const sse_io *ios, int32_t n, int32_t *tiles_per_unit,
+                            int32_t *longest_first) {
+    sse_status st = check_batch(plans, ios, n);
+    if (st != SSE_OK) return st;
+    if (!tiles_per_unit || !longest_first) return set_error("output pointers are NULL"), SSE_E_INVALID_ARG;
+    std::vector<Plan *> ps((size_t)n);
+    for (int32_t i = 0; i < n; ++i) ps[i] = plans[i];
+    int tpc = 0, lpt = 0;
+    if (!batch_choice(ps.data(), ios, n, &tpc, &lpt)) return SSE_NOT_READY;
+    *tiles_per_unit = tpc;
+    *longest_first = lpt;
     return SSE_OK;
 }
 

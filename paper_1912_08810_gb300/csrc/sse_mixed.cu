@@ -56,19 +56,33 @@ struct Geo {
     static constexpr int A_PLANE = (kRowsMax / 8) * SBO_A;
 };
 
-struct MixParams {
-    const int32_t *neigh;
-    const void *dH;
+constexpr int kMaxInst = 64;  // instances per launch (the descriptors travel as kernel parameters)
+
+// One independent SSE instance of a launch.  Its work is split into units
+// (sign, atom, range of tiles); units are numbered from unit_begin.
+struct InstDesc {
     const void *G[2];
     const void *D[2];
     void *S[2];
-    int32_t *status;
-    Dims d;
-    int nst;            // stages per job
-    int ntiles;         // tiles per atom
-    int tiles_per_cta;
-    int nchunks;        // CTAs per (sign, atom)
+    const void *dH;
+    const int32_t *neigh;
+    int32_t na, ne, nb, nqz;
+    int32_t ntiles;         // tiles per atom
+    int32_t tiles_per_cta;  // tiles per unit
+    int32_t nchunks;        // units per (sign, atom)
+    int32_t nsign;
+    long long unit_begin;
+};
+
+struct MixParams {
+    int32_t *status;        // device status word (bounded waits that expired)
+    int32_t *queue;         // work counter of a persistent launch; null: unit = blockIdx.x
+    int32_t nkz, nw, omega_first;
+    int32_t nst;            // stages per job
+    int32_t n_inst;
+    long long total_units;
     uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, g_stage;
+    InstDesc inst[kMaxInst];
 };
 
 __device__ __forceinline__ float2 cmul_conj_acc(float2 acc, float2 v, float2 h) {
@@ -78,6 +92,22 @@ __device__ __forceinline__ float2 cmul_conj_acc(float2 acc, float2 v, float2 h) 
     acc.y = fmaf(v.y, h.x, acc.y);
     acc.y = fmaf(-v.x, h.y, acc.y);
     return acc;
+}
+
+// (hi, lo) bf16 splits of two floats, packed: .x = (hi(a), hi(b)), .y = (lo(a), lo(b)),
+// the first value in the low half of each word.
+__device__ __forceinline__ uint2 split2_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    return make_uint2(*reinterpret_cast<const uint32_t *>(&h), *reinterpret_cast<const uint32_t *>(&l));
+}
+
+// Each word holds a (re-part, im-part) K pair (Re T, -Im T); the imaginary-part accumulator
+// needs (Im T, Re T): swap the halves and flip the sign of the new low half.
+__device__ __forceinline__ uint32_t to_im_pair(uint32_t w) { return __byte_perm(w, 0u, 0x1032) ^ 0x00008000u; }
+__device__ __forceinline__ uint4 to_im_pairs(uint4 v) {
+    return make_uint4(to_im_pair(v.x), to_im_pair(v.y), to_im_pair(v.z), to_im_pair(v.w));
 }
 
 template <typename CT>
@@ -105,26 +135,22 @@ __device__ __forceinline__ void rmw_store<float2>(float2 *dst, float2 v, bool fi
 }
 
 template <int NK, typename CT>
-__global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams prm) {
+__global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_constant__ MixParams prm) {
     using GG = Geo<NK>;
     extern __shared__ __align__(1024) uint8_t smem[];
-    const Dims d = prm.d;
-    const int sign = blockIdx.y;
-    const CT *__restrict__ G = (const CT *)prm.G[sign];
-    const CT *__restrict__ D = (const CT *)prm.D[sign];
-    CT *__restrict__ S = (CT *)prm.S[sign];
-    const CT *__restrict__ dH = (const CT *)prm.dH;
-    const int a = blockIdx.x / prm.nchunks, chunk = blockIdx.x % prm.nchunks;
-    const int t_begin = chunk * prm.tiles_per_cta;
-    const int t_end = min(prm.ntiles, t_begin + prm.tiles_per_cta);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nw = d.nw;
-    const int omega_max = d.omega_first + nw - 1;
+    const int nw = prm.nw;
+    const int omega_max = prm.omega_first + nw - 1;
+    const int nw0 = nw + GG::P - 1;                   // rows of the table per (k, j)
+    constexpr uint32_t tab_stride = GG::KST * 4 + 16;  // hi + lo + 16 bytes against bank conflicts
+    // (k, j) groups of rows: padded so that consecutive groups -- read by consecutive lanes --
+    // start 16 bytes apart modulo 128 and the 16-byte loads of 8 lanes hit distinct banks
+    const uint32_t grp_stride = ((uint32_t)nw0 * tab_stride + 127u) / 128u * 128u + 16u;
 
     uint8_t *sB = smem + prm.off_b;                 // [2 stages][hi, lo] B planes
     uint8_t *sA = smem + prm.off_a;                 // [2 stages][re, im][hi, lo] A planes
     uint8_t *sG = smem + prm.off_g;                 // [2 stages] raw G blocks
-    uint32_t *sDf = (uint32_t *)(smem + prm.off_df);  // [k][k'][w][ij][re, im] split words
+    uint8_t *sTab = smem + prm.off_df;                // Toeplitz row table of the current slot
     float2 *sDh = (float2 *)(smem + prm.off_dh);      // [3][144] fp32 dH of the current slot
     float *sV = (float *)(smem + prm.off_b);          // drained accumulators (overlays B and A)
     uint64_t *bar_mma = (uint64_t *)(smem + prm.off_bar);
@@ -134,7 +160,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
     uint32_t *s_tmem = (uint32_t *)(bar_mma + 6);
     int *s_abort = (int *)(s_tmem + 1);
     int *s_nvalid = s_abort + 1;
-    int *s_slot = s_nvalid + 1;                       // [kMaxSlots] valid slot indices
+    long long *s_unit = (long long *)(smem + prm.off_bar + 64);
+    int *s_slot = (int *)(s_unit + 1);                // [kMaxSlots] valid slot indices
     int *s_f = s_slot + kMaxSlots;                    // [kMaxSlots] their neighbour atoms
 
     if (tid == 0) {
@@ -146,16 +173,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
         mbar_init(bar_fin, 1);
         fence_mbar_init();
         *s_abort = 0;
-        int nv = 0;
-        for (int b = 0; b < d.nb && nv < kMaxSlots; ++b) {
-            const int f = __ldg(prm.neigh + (size_t)a * d.nb + b);
-            if (f >= 0) {
-                s_slot[nv] = b;
-                s_f[nv] = f;
-                ++nv;
-            }
-        }
-        *s_nvalid = nv;
     }
     if (warp == 0) {
         tmem_alloc(s_tmem, kTmemCols);
@@ -165,12 +182,62 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
+
+    // Per-thread A-builder row: thread -> (accumulator q, row m).
+    const int aq = tid >> 7, am = tid & 127;
+    const bool arow_ok = am < GG::ROWS;
+    const int ae = am / (3 * NK), ak = (am / 3) % NK, aj = am % 3;
+
+    bool abort = false;
+    int abort_g = -1, abort_total = 0;
+    int g_base = 0, job_base = 0;  // stages and jobs this CTA ran before the current unit
+    for (long long iter = 0;; ++iter) {
+    // ---- next unit: one per CTA, or pulled from the work counter ----
+    __syncthreads();
+    if (tid == 0) {
+        long long u;
+        if (prm.queue) u = atomicAdd(prm.queue, 1);
+        else u = iter == 0 ? (long long)blockIdx.x : prm.total_units;
+        if (*(volatile int32_t *)prm.status != 0) u = prm.total_units;  // another CTA timed out
+        *s_unit = u;
+    }
+    __syncthreads();
+    const long long unit = *s_unit;
+    if (unit >= prm.total_units) break;
+    int ii = 0;
+    while (ii + 1 < prm.n_inst && prm.inst[ii + 1].unit_begin <= unit) ++ii;
+    const InstDesc &I = prm.inst[ii];
+    const long long local = unit - I.unit_begin;
+    const int sign = (int)(local / ((long long)I.na * I.nchunks));
+    const long long rem = local - (long long)sign * I.na * I.nchunks;
+    const int a = (int)(rem / I.nchunks), chunk = (int)(rem % I.nchunks);
+    const Dims d{prm.nkz, I.nqz, I.ne, nw, I.na, I.nb, prm.omega_first};
+    const CT *__restrict__ G = (const CT *)I.G[sign];
+    const CT *__restrict__ D = (const CT *)I.D[sign];
+    CT *__restrict__ S = (CT *)I.S[sign];
+    const CT *__restrict__ dH = (const CT *)I.dH;
+    const int t_begin = chunk * I.tiles_per_cta;
+    const int t_end = min(I.ntiles, t_begin + I.tiles_per_cta);
+
+    if (tid == 0) {
+        int nv = 0;
+        for (int b = 0; b < d.nb && nv < kMaxSlots; ++b) {
+            const int f = __ldg(I.neigh + (size_t)a * d.nb + b);
+            if (f >= 0) {
+                s_slot[nv] = b;
+                s_f[nv] = f;
+                ++nv;
+            }
+        }
+        *s_nvalid = nv;
+    }
+    __syncthreads();
     const int nvalid = *s_nvalid;
     const int njobs = (t_end - t_begin) * nvalid;
     const int total = njobs * prm.nst;
 
     if (nvalid == 0) {
-        // no neighbours: Sigma is zero on this CTA's points
+        // no neighbours: Sigma is zero on this unit's points
         for (int t = t_begin; t < t_end; ++t)
             for (int x = tid; x < NK * GG::TE * kCh; x += kThreads) {
                 const int e = x / (NK * kCh), k = (x / kCh) % NK, c = x % kCh;
@@ -203,9 +270,10 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
             const int Ep = e_first + p;
             if (Ep >= 0 && Ep < d.ne) bytes += NK * kCh * (uint32_t)sizeof(CT);
         }
-        uint64_t *bar = &bar_g[g & 1];
+        const int gg = g_base + g;
+        uint64_t *bar = &bar_g[gg & 1];
         mbar_arrive_expect_tx(bar, bytes);
-        uint8_t *dst = sG + (g & 1) * prm.g_stage;
+        uint8_t *dst = sG + (gg & 1) * prm.g_stage;
 #pragma unroll
         for (int p = 0; p < GG::P; ++p) {
             const int Ep = e_first + p;
@@ -216,21 +284,15 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
         }
     };
 
-    // Per-thread A-builder row: thread -> (accumulator q, row m).
-    const int aq = tid >> 7, am = tid & 127;
-    const bool arow_ok = am < GG::ROWS;
-    const int ae = am / (3 * NK), ak = (am / 3) % NK, aj = am % 3;
-
     if (tid == 0 && total > 0) issue_g(0);
 
-    bool abort = false;
-    int abort_g = -1;
     for (int g = 0; g < total && !abort; ++g) {
         int t, vs, st;
         decode(g, t, vs, st);
-        const int sb = g & 1;
+        const int gg = g_base + g;  // CTA-wide stage index: buffer and barrier phases
+        const int sb = gg & 1;
         const int E0 = t * GG::TE;
-        const int job = g / prm.nst;
+        const int job = job_base + g / prm.nst;
         const bool job_first = st == 0, job_last = st == prm.nst - 1;
 
         if (job_first) {
@@ -239,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
             const int b = s_slot[vs];
             const CT *dh = dH + ((size_t)a * d.nb + b) * 3 * kCh;
             for (int x = tid; x < 3 * kCh; x += kThreads) sDh[x] = load_c32(dh + x);
-            uint32_t *tmp = (uint32_t *)sB;  // [kappa][w][ij][re, im]
+            float2 *dfold = (float2 *)sB;  // [kappa][w][ij] folded Dt (fp32), A/B area as scratch
             for (int x = tid; x < NK * nw * 9; x += kThreads) {
                 const int ij = x % 9, w = (x / 9) % nw, kap = x / (9 * nw);
                 // fold qz onto kz' = qz mod Nkz: T depends on (k - k') mod Nkz only
@@ -249,16 +311,42 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
                     acc.x += v.x;
                     acc.y += v.y;
                 }
-                tmp[2 * x] = split_bf16(acc.x);
-                tmp[2 * x + 1] = split_bf16(acc.y);
+                dfold[x] = acc;
             }
             __syncthreads();
-            for (int x = tid; x < NK * NK * nw * 9; x += kThreads) {
-                const int ij = x % 9, w = (x / 9) % nw, kp = (x / (9 * nw)) % NK, k = x / (9 * nw * NK);
-                const int kap = (k - kp + NK) % NK;
-                const int src = (kap * nw + w) * 9 + ij;
-                sDf[2 * x] = tmp[2 * src];
-                sDf[2 * x + 1] = tmp[2 * src + 1];
+            // Row table of the real-part accumulator's Toeplitz operand: one row per
+            // (k, j, w0), w0 in [0, nw0); entry (p, i, k', re/im) = (Re T, -Im T) with
+            // T = Df_ij[(k - k') mod Nkz][w0 - p]; bf16 hi plane then lo plane.  A tile row
+            // (e, k, j) of stage st is the row w0 = e + nw - 1 - P * st.
+            for (int x = tid; x < 3 * NK * nw0 * (GG::KST / 8); x += kThreads) {
+                const int gq = x % (GG::KST / 8), row = x / (GG::KST / 8);
+                const int w0 = row % nw0, kj = row / nw0, k = kj / 3, j = kj % 3;
+                uint32_t hv[4], lv[4];
+#pragma unroll
+                for (int xx = 0; xx < 8; xx += 2) {
+                    float v2[2];
+#pragma unroll
+                    for (int y = 0; y < 2; ++y) {
+                        const int kk = gq * 8 + xx + y;
+                        const int pp = kk / GG::KS, r2 = kk % GG::KS;
+                        float v = 0.f;
+                        if (r2 < 6 * NK) {
+                            const int pair = r2 >> 1, pc = r2 & 1, i = pair / NK, kp = pair % NK;
+                            const int w = w0 - pp;
+                            if (w >= 0 && w < nw) {
+                                const float2 T = dfold[(((k - kp + NK) % NK) * nw + w) * 9 + i * 3 + j];
+                                v = pc ? -T.y : T.x;
+                            }
+                        }
+                        v2[y] = v;
+                    }
+                    const uint2 hl = split2_bf16(v2[0], v2[1]);
+                    hv[xx / 2] = hl.x;
+                    lv[xx / 2] = hl.y;
+                }
+                uint8_t *trow = sTab + (size_t)kj * grp_stride + (size_t)w0 * tab_stride;
+                *(uint4 *)(trow + gq * 16) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                *(uint4 *)(trow + GG::KST * 2 + gq * 16) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
             }
             __syncthreads();
         }
@@ -268,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
         if (tid == 0 && g + 1 < total) issue_g(g + 1);
 
         // ---- G blocks of this stage: wait, convert to fp32 in place, zero the gaps ----
-        if (!mbar_wait_bounded(&bar_g[sb], (g >> 1) & 1, kWaitNs)) {
+        if (!mbar_wait_bounded(&bar_g[sb], (gg >> 1) & 1, kWaitNs)) {
             *s_abort = 1;
             atomicExch(prm.status, 1);
         }
@@ -304,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
         }
 
         // ---- the stage buffers must be free: MMAs of stage g - 2 complete ----
-        if (g >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((g >> 1) - 1) & 1, kWaitNs)) {
+        if (gg >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((gg >> 1) - 1) & 1, kWaitNs)) {
             *s_abort = 1;
             atomicExch(prm.status, 1);
         }
@@ -322,27 +410,31 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
                 hw[x] = 0u;
                 lw[x] = 0u;
             }
+            float2 hrow[3][12];  // dH_i[r, :] for the three directions
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float2 hrow[12];
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int u = 0; u < 12; ++u) hrow[u] = sDh[i * kCh + r * 12 + u];
+                for (int u = 0; u < 12; ++u) hrow[i][u] = sDh[i * kCh + r * 12 + u];
 #pragma unroll
-                for (int kp = 0; kp < NK; ++kp) {
-                    const float2 *gcol = g32 + (p * NK + kp) * kCh + tt;
-                    float xr = 0.f, xi = 0.f;
+            for (int kp = 0; kp < NK; ++kp) {
+                const float2 *gcol = g32 + (p * NK + kp) * kCh + tt;
+                float xr[3] = {0.f, 0.f, 0.f}, xi[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int u = 0; u < 12; ++u) {
-                        const float2 gv = gcol[u * 12];
-                        xr = fmaf(hrow[u].x, gv.x, xr);
-                        xr = fmaf(-hrow[u].y, gv.y, xr);
-                        xi = fmaf(hrow[u].x, gv.y, xi);
-                        xi = fmaf(hrow[u].y, gv.x, xi);
+                for (int u = 0; u < 12; ++u) {
+                    const float2 gv = gcol[u * 12];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        xr[i] = fmaf(hrow[i][u].x, gv.x, xr[i]);
+                        xr[i] = fmaf(-hrow[i][u].y, gv.y, xr[i]);
+                        xi[i] = fmaf(hrow[i][u].x, gv.y, xi[i]);
+                        xi[i] = fmaf(hrow[i][u].y, gv.x, xi[i]);
                     }
-                    const uint32_t sr = split_bf16(xr), si = split_bf16(xi);
-                    const int pair = i * NK + kp;  // K index 2 * pair (re), 2 * pair + 1 (im)
-                    hw[pair] = __byte_perm(sr, si, 0x5410);
-                    lw[pair] = __byte_perm(sr, si, 0x7632);
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const uint2 hl = split2_bf16(xr[i], xi[i]);  // K index 2 * pair (re), 2 * pair + 1 (im)
+                    hw[i * NK + kp] = hl.x;
+                    lw[i * NK + kp] = hl.y;
                 }
             }
             const uint32_t row_off = (n >> 3) * GG::SBO_B + (n & 7) * 16 + (p * GG::KS / 8) * 128;
@@ -353,38 +445,26 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
             }
         }
 
-        // ---- Toeplitz slice: A_q[(e, k, j), (p, i, k', re/im)] ----
+        // ---- Toeplitz slice: A_q[(e, k, j), (p, i, k', re/im)] copied from the row table ----
         {
             uint8_t *ahi = abase + aq * (2 * GG::A_PLANE), *alo = ahi + GG::A_PLANE;
             const uint32_t row_off = (am >> 3) * GG::SBO_A + (am & 7) * 16;
-            const int wrow = ae + nw - 1 - GG::P * st;  // w for p = 0
-            const uint32_t *dfrow = sDf + ((size_t)ak * NK * nw * 9 + aj) * 2;
+            const int w0 = ae + nw - 1 - GG::P * st;
+            const bool live = arow_ok && w0 >= 0 && w0 < nw0;
+            const uint8_t *trow = sTab + (size_t)(ak * 3 + aj) * grp_stride + (size_t)(live ? w0 : 0) * tab_stride;
 #pragma unroll
             for (int gq = 0; gq < GG::KST / 8; ++gq) {
-                uint32_t wv[8];
-#pragma unroll
-                for (int x = 0; x < 8; ++x) {
-                    const int kk = gq * 8 + x;
-                    const int p = kk / GG::KS, r2 = kk % GG::KS;
-                    uint32_t val = 0u;
-                    if (r2 < 6 * NK && arow_ok) {
-                        const int pair = r2 >> 1, pc = r2 & 1;
-                        const int i = pair / NK, kp = pair % NK;
-                        const int w = wrow - p;
-                        if (w >= 0 && w < nw) {
-                            const int use_im = aq ^ pc;
-                            val = dfrow[(((size_t)kp * nw + w) * 9 + i * 3) * 2 + use_im];
-                            if (aq == 0 && pc == 1) val ^= 0x80008000u;
-                        }
+                uint4 h = make_uint4(0u, 0u, 0u, 0u), l = h;
+                if (live) {
+                    h = *(const uint4 *)(trow + gq * 16);
+                    l = *(const uint4 *)(trow + GG::KST * 2 + gq * 16);
+                    if (aq) {  // imaginary-part accumulator: (Im T, Re T) from (Re T, -Im T)
+                        h = to_im_pairs(h);
+                        l = to_im_pairs(l);
                     }
-                    wv[x] = val;
                 }
-                const uint4 h4 = make_uint4(__byte_perm(wv[0], wv[1], 0x5410), __byte_perm(wv[2], wv[3], 0x5410),
-                                            __byte_perm(wv[4], wv[5], 0x5410), __byte_perm(wv[6], wv[7], 0x5410));
-                const uint4 l4 = make_uint4(__byte_perm(wv[0], wv[1], 0x7632), __byte_perm(wv[2], wv[3], 0x7632),
-                                            __byte_perm(wv[4], wv[5], 0x7632), __byte_perm(wv[6], wv[7], 0x7632));
-                *(uint4 *)(ahi + row_off + gq * 128) = h4;
-                *(uint4 *)(alo + row_off + gq * 128) = l4;
+                *(uint4 *)(ahi + row_off + gq * 128) = h;
+                *(uint4 *)(alo + row_off + gq * 128) = l;
             }
         }
 
@@ -392,7 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
         __syncthreads();
         if (*s_abort) {
             abort = true;
-            abort_g = g;
+            abort_g = gg;
+            abort_total = g_base + total;
             break;
         }
 
@@ -489,10 +570,15 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
         __syncthreads();
         if (*s_abort) {
             abort = true;
-            abort_g = g;
+            abort_g = gg;
+            abort_total = g_base + total;
             break;
         }
     }
+    g_base += total;
+    job_base += njobs;
+    if (abort) break;
+    }  // units
 
     // ---- teardown: nothing of ours may still be in flight when the CTA exits ----
     if (abort) {
@@ -500,7 +586,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const MixParams 
         mbar_wait_bounded(bar_fin, 0, kWaitNs);
         // the bulk copies of the aborted stage and of the one prefetched after it
         if (abort_g >= 0) mbar_wait_bounded(&bar_g[abort_g & 1], (abort_g >> 1) & 1, kWaitNs);
-        if (abort_g + 1 < total) mbar_wait_bounded(&bar_g[(abort_g + 1) & 1], ((abort_g + 1) >> 1) & 1, kWaitNs);
+        if (abort_g + 1 < abort_total)
+            mbar_wait_bounded(&bar_g[(abort_g + 1) & 1], ((abort_g + 1) >> 1) & 1, kWaitNs);
     }
     tc_fence_before();
     __syncthreads();
@@ -525,64 +612,128 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
     prm.off_a = prm.off_b + 2 * 2 * GG::B_PLANE;
     prm.g_stage = (uint32_t)(GG::P * NK * kCh * cbytes);
     prm.off_g = take(2 * prm.g_stage, 128);
-    const uint32_t dfr = (uint32_t)(NK * NK * d.nw * 9 * 8);
+    const uint32_t grp = ((uint32_t)(d.nw + GG::P - 1) * (GG::KST * 4 + 16) + 127u) / 128u * 128u + 16u;
+    const uint32_t tab = (uint32_t)(3 * NK) * grp;
     const uint32_t dtmp = (uint32_t)(NK * d.nw * 9 * 8);
-    prm.off_df = take(dfr, 16);
+    prm.off_df = take(tab, 16);
     prm.off_dh = take(3 * kCh * 8, 16);
-    prm.off_bar = take(6 * 8 + 4 + 4 + 4 + 2 * kMaxSlots * 4, 8);
+    prm.off_bar = take(64 + 8 + 2 * kMaxSlots * 4, 8);
     if (dtmp > (ab > need_v ? ab : need_v)) return 0xFFFFFFFFu;
     return off;
+}
+
+// One instance descriptor from a plan and its buffers; the requested signs are packed
+// into slots 0 and 1.  Returns false when no sign is requested.
+template <int NK>
+bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc) {
+    using GG = Geo<NK>;
+    const bool do_gt = io.S_gt != nullptr, do_lt = io.S_lt != nullptr;
+    I.nsign = (int)do_gt + (int)do_lt;
+    if (I.nsign == 0) return false;
+    I.G[0] = do_gt ? io.G_gt : io.G_lt;
+    I.D[0] = do_gt ? io.D_gt : io.D_lt;
+    I.S[0] = do_gt ? io.S_gt : io.S_lt;
+    I.G[1] = io.G_lt;
+    I.D[1] = io.D_lt;
+    I.S[1] = io.S_lt;
+    I.dH = p.geo.dH;
+    I.neigh = p.geo.neigh;
+    I.na = p.d.na;
+    I.ne = p.d.ne;
+    I.nb = p.d.nb;
+    I.nqz = p.d.nqz;
+    I.ntiles = (I.ne + GG::TE - 1) / GG::TE;
+    I.tiles_per_cta = tpc < 1 ? 1 : (tpc > I.ntiles ? I.ntiles : tpc);
+    I.nchunks = (I.ntiles + I.tiles_per_cta - 1) / I.tiles_per_cta;
+    return true;
+}
+
+long long inst_units(const InstDesc &I) { return (long long)I.nsign * I.na * I.nchunks; }
+
+template <int NK, typename CT>
+sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *status) {
+    using GG = Geo<NK>;
+    smem = mixed_smem_bytes<NK>(d, sizeof(CT), prm);
+    if (smem > 232448u) {
+        set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
+        return SSE_E_INVALID_ARG;
+    }
+    prm.status = status;
+    prm.nkz = d.nkz;
+    prm.nw = d.nw;
+    prm.omega_first = d.omega_first;
+    prm.nst = (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
+    cudaError_t e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed kernel)");
+    return SSE_OK;
+}
+
+bool aligned16(const sse_io &io) {
+    return ((((uintptr_t)io.G_gt | (uintptr_t)io.G_lt)) & 15u) == 0;
 }
 
 template <int NK, typename CT>
 sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     using GG = Geo<NK>;
     MixParams prm{};
-    const Dims &d = p.d;
-    const uint32_t smem = mixed_smem_bytes<NK>(d, sizeof(CT), prm);
-    if (smem > 232448u) {
-        set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
-        return SSE_E_INVALID_ARG;
-    }
-    if (((uintptr_t)io.G_gt | (uintptr_t)io.G_lt) & 15u) {
-        set_error("mixed mode: G buffers must be 16-byte aligned");
-        return SSE_E_INVALID_ARG;
-    }
-    prm.neigh = p.geo.neigh;
-    prm.dH = p.geo.dH;
-    prm.status = p.d_status;
-    prm.d = d;
-    prm.ntiles = (d.ne + GG::TE - 1) / GG::TE;
-    prm.nst = (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
-    const bool do_gt = io.S_gt != nullptr, do_lt = io.S_lt != nullptr;
-    const int nsign = (int)do_gt + (int)do_lt;
-    if (nsign == 0) return SSE_OK;
-    prm.G[0] = do_gt ? io.G_gt : io.G_lt;
-    prm.D[0] = do_gt ? io.D_gt : io.D_lt;
-    prm.S[0] = do_gt ? io.S_gt : io.S_lt;
-    prm.G[1] = io.G_lt;
-    prm.D[1] = io.D_lt;
-    prm.S[1] = io.S_lt;
-    // tiles per CTA: enough CTAs for several waves over the SMs, at least 1 tile each
+    uint32_t smem = 0;
+    sse_status rs = prepare<NK, CT>(prm, smem, p.d, p.d_status);
+    if (rs != SSE_OK) return rs;
+    if (!aligned16(io)) return set_error("mixed mode: G buffers must be 16-byte aligned"), SSE_E_INVALID_ARG;
+    // tiles per unit: enough units for several waves over the SMs
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-    const long long units = (long long)nsign * d.na;
-    int tpc = prm.ntiles;
-    while (tpc > 1 && units * ((prm.ntiles + tpc - 1) / tpc) < 8LL * sms) tpc = (tpc + 1) / 2;
-    prm.tiles_per_cta = tpc;
-    prm.nchunks = (prm.ntiles + tpc - 1) / tpc;
-    const long long gx = (long long)d.na * prm.nchunks;
-    if (gx > 0x7fffffffLL) {
-        set_error("mixed mode: grid too large");
-        return SSE_E_INVALID_ARG;
-    }
-    auto kern = sse_mixed_kernel<NK, CT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed kernel)");
-    kern<<<dim3((unsigned)gx, nsign), kThreads, smem, st>>>(prm);
-    e = cudaGetLastError();
+    const int ntiles = (p.d.ne + GG::TE - 1) / GG::TE;
+    const long long per_chunk = (long long)((io.S_gt != nullptr) + (io.S_lt != nullptr)) * p.d.na;
+    int tpc = ntiles;
+    while (tpc > 1 && per_chunk * ((ntiles + tpc - 1) / tpc) < 8LL * sms) tpc = (tpc + 1) / 2;
+    if (!fill_inst<NK>(prm.inst[0], p, io, tpc)) return SSE_OK;
+    prm.n_inst = 1;
+    prm.inst[0].unit_begin = 0;
+    prm.total_units = inst_units(prm.inst[0]);
+    prm.queue = nullptr;
+    if (prm.total_units > 0x7fffffffLL) return set_error("mixed mode: grid too large"), SSE_E_INVALID_ARG;
+    sse_mixed_kernel<NK, CT><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch sse_mixed_kernel");
     p.tile_e = GG::TE;
+    return SSE_OK;
+}
+
+// Persistent launches over many instances: one CTA per SM pulls units from a counter.
+template <int NK, typename CT>
+sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
+                           int32_t *queue, cudaStream_t st) {
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plans[0]->device);
+    for (int base = 0; base < n; base += kMaxInst) {
+        MixParams prm{};
+        uint32_t smem = 0;
+        sse_status rs = prepare<NK, CT>(prm, smem, plans[order[base]]->d, plans[order[base]]->d_status);
+        if (rs != SSE_OK) return rs;
+        long long units = 0;
+        int m = 0;
+        for (int x = base; x < n && x < base + kMaxInst; ++x) {
+            const Plan &p = *plans[order[x]];
+            const sse_io &io = ios[order[x]];
+            if (!aligned16(io)) return set_error("mixed mode: G buffers must be 16-byte aligned"), SSE_E_INVALID_ARG;
+            if (!fill_inst<NK>(prm.inst[m], p, io, tpc)) continue;
+            prm.inst[m].unit_begin = units;
+            units += inst_units(prm.inst[m]);
+            ++m;
+        }
+        if (m == 0) continue;
+        prm.n_inst = m;
+        prm.total_units = units;
+        prm.queue = queue;
+        cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "reset the work counter");
+        const long long grid = units < sms ? units : sms;
+        sse_mixed_kernel<NK, CT><<<(unsigned)grid, kThreads, smem, st>>>(prm);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "launch persistent sse_mixed_kernel");
+    }
     return SSE_OK;
 }
 
@@ -596,6 +747,21 @@ sse_status launch_dtype(Plan &p, const sse_io &io, cudaStream_t st) {
         case 5: return launch_nk<5, CT>(p, io, st);
         default:
             set_error("mixed mode supports Nkz <= 5 (got %d)", p.d.nkz);
+            return SSE_E_INVALID_ARG;
+    }
+}
+
+template <typename CT>
+sse_status launch_batch_dtype(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
+                              int32_t *queue, cudaStream_t st) {
+    switch (plans[order[0]]->d.nkz) {
+        case 1: return launch_batch_nk<1, CT>(plans, ios, order, n, tpc, queue, st);
+        case 2: return launch_batch_nk<2, CT>(plans, ios, order, n, tpc, queue, st);
+        case 3: return launch_batch_nk<3, CT>(plans, ios, order, n, tpc, queue, st);
+        case 4: return launch_batch_nk<4, CT>(plans, ios, order, n, tpc, queue, st);
+        case 5: return launch_batch_nk<5, CT>(plans, ios, order, n, tpc, queue, st);
+        default:
+            set_error("mixed mode supports Nkz <= 5");
             return SSE_E_INVALID_ARG;
     }
 }
@@ -639,6 +805,13 @@ void mixed_plan_free(Plan &p) { (void)p; }
 sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st) {
     if (p.geo.dtype == SSE_C128) return launch_dtype<double2>(p, io, st);
     return launch_dtype<float2>(p, io, st);
+}
+
+sse_status launch_mixed_batch(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
+                              int32_t *queue, cudaStream_t st) {
+    if (n <= 0) return SSE_OK;
+    if (plans[order[0]]->geo.dtype == SSE_C128) return launch_batch_dtype<double2>(plans, ios, order, n, tpc, queue, st);
+    return launch_batch_dtype<float2>(plans, ios, order, n, tpc, queue, st);
 }
 
 }  // namespace sse

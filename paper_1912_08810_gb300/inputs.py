@@ -204,3 +204,67 @@ def make_batched(spec: BatchedSpec, seed: int, *, dtype=np.complex64,
         inst["geometry"] = g
         out.append(inst)
     return out
+
+
+def make_instance_torch(geo: Geometry, seed: int, *, device="cuda", dtype=None,
+                        neigh: Optional[np.ndarray] = None, hermitian_pairs: Optional[bool] = None):
+    """Same recipe as make_instance, drawn on the device with torch's counter-based
+    generator (for workloads too large to draw on the host).  Values differ from the
+    numpy draw of the same seed; tests that compare with the CPU oracle copy these
+    tensors to the host, so both sides still consume the same bytes.  Returns a dict of
+    torch tensors (complex64 by default)."""
+    import torch
+    dtype = dtype or torch.complex64
+    real = torch.float32 if dtype == torch.complex64 else torch.float64
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    if neigh is None:
+        if geo.nb != len(CHAIN_OFFSETS):
+            raise ValueError("default chain neighbours need nb == 4")
+        neigh = chain_neighbours(geo.na)
+        if hermitian_pairs is None:
+            hermitian_pairs = True
+    neigh_np = np.ascontiguousarray(neigh, dtype=np.int32)
+
+    def cnormal(shape):
+        x = torch.randn(tuple(shape) + (2,), generator=gen, device=device, dtype=real)
+        return torch.view_as_complex(x)
+
+    def anti_herm(shape):
+        a = cnormal(shape)
+        return (a - a.transpose(-1, -2).conj()).contiguous()
+
+    def herm(shape):
+        b = cnormal(shape)
+        return (b + b.transpose(-1, -2).conj()).contiguous()
+
+    lead_g = (geo.nkz, geo.ne, geo.na, geo.norb, geo.norb)
+    out = {"G_gt": anti_herm(lead_g), "G_lt": anti_herm(lead_g)}
+    dh = cnormal((geo.na, geo.nb, N3D, geo.norb, geo.norb))
+    if hermitian_pairs:
+        dh_np = dh.cpu().numpy()
+        _make_reverse_bonds_hermitian(dh_np, neigh_np)
+        dh = torch.from_numpy(dh_np).to(device)
+    out["dH"] = dh.contiguous()
+    lead_d = (geo.nqz, geo.nw, geo.na, geo.nb, N3D, N3D)
+    out["D_gt"] = herm(lead_d)
+    out["D_lt"] = herm(lead_d)
+    out["neigh"] = torch.from_numpy(neigh_np).to(device)
+    return out
+
+
+def make_batched_torch(spec: BatchedSpec, seed: int, *, device="cuda", which: Optional[List[int]] = None):
+    """The batched workload drawn on the device: instance i uses neighbour lists from
+    numpy seed (seed, i, 1) (as make_batched) and values from torch seed (seed, i, 2)."""
+    geos = batched_geometries(spec, seed)
+    idx = range(len(geos)) if which is None else which
+    out = []
+    for i in idx:
+        g = geos[i]
+        nrng = np.random.default_rng([seed, i, 1])
+        neigh = random_neighbours(nrng, g.na, spec.nb_max, spec.nb_range[0], spec.nb_range[1], spec.reach)
+        vseed = int(np.random.SeedSequence([seed, i, 2]).generate_state(1)[0])
+        inst = make_instance_torch(g, vseed, device=device, neigh=neigh, hermitian_pairs=False)
+        inst["geometry"] = g
+        out.append(inst)
+    return out

@@ -37,7 +37,8 @@ SSE_MODE_MIXED = 1
 EXPORTED = (
     "sse_plan", "sse_plan_destroy", "sse_plan_query", "sse_execute", "sse_execute_host",
     "sse_plan_status", "sse_status_string", "sse_last_error", "sse_abi_version",
-    "sse_execute_noalloc",
+    "sse_execute_noalloc", "sse_execute_batch", "sse_batch_tuning",
+    "sse_server_create", "sse_submit", "sse_poll", "sse_server_destroy", "sse_server_stats",
 )
 
 
@@ -60,6 +61,11 @@ class sse_plan_info(ctypes.Structure):
                 ("flops_per_sign", ctypes.c_double), ("bytes_per_sign", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("tile_e", ctypes.c_int32),
                 ("kernel_id", ctypes.c_int32)]
+
+
+class sse_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_end_ms", ctypes.c_double), ("round_size", ctypes.c_int32)]
 
 
 class SSEError(RuntimeError):
@@ -94,6 +100,15 @@ def load(path: Optional[str] = None):
             "sse_last_error": ([], ctypes.c_char_p),
             "sse_abi_version": ([], st),
             "sse_execute_noalloc": ([ctypes.POINTER(sse_geometry), ctypes.POINTER(sse_io), vp], st),
+            "sse_execute_batch": ([ctypes.POINTER(vp), ctypes.POINTER(sse_io), ctypes.c_int32, vp], st),
+            "sse_batch_tuning": ([ctypes.POINTER(vp), ctypes.POINTER(sse_io), ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], st),
+            "sse_server_create": ([ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(vp)], st),
+            "sse_submit": ([vp, vp, ctypes.POINTER(sse_io), ctypes.POINTER(ctypes.c_uint64)], st),
+            "sse_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(sse_result)], st),
+            "sse_server_destroy": ([vp], st),
+            "sse_server_stats": ([vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                  ctypes.POINTER(ctypes.c_int32)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -151,6 +166,59 @@ def sse_execute_noalloc(geo: sse_geometry, io: sse_io, stream: int = 0) -> None:
     """Mixed-mode evaluation that allocates nothing (see include/sse.h); synchronous."""
     _check(load().sse_execute_noalloc(ctypes.byref(geo), ctypes.byref(io), ctypes.c_void_p(stream)),
            "sse_execute_noalloc")
+
+
+def _batch_args(plans, ios):
+    n = len(plans)
+    parr = (ctypes.c_void_p * max(n, 1))(*[p.value if hasattr(p, "value") else p for p in plans])
+    iarr = (sse_io * max(n, 1))(*ios)
+    return parr, iarr, n
+
+
+def sse_execute_batch(plans, ios, stream: int = 0) -> None:
+    """Many instances in one persistent launch (plan handles and sse_io structs)."""
+    parr, iarr, n = _batch_args(plans, ios)
+    _check(load().sse_execute_batch(parr, iarr, n, ctypes.c_void_p(stream)), "sse_execute_batch")
+
+
+def sse_batch_tuning(plans, ios):
+    """(tiles_per_unit, longest_first) chosen by the autotuner, or None if not tuned yet."""
+    parr, iarr, n = _batch_args(plans, ios)
+    tpc, lpt = ctypes.c_int32(), ctypes.c_int32()
+    rc = _check(load().sse_batch_tuning(parr, iarr, n, ctypes.byref(tpc), ctypes.byref(lpt)), "sse_batch_tuning")
+    return None if rc == SSE_NOT_READY else (tpc.value, lpt.value)
+
+
+def sse_server_create(mem_budget_bytes: int, max_inflight: int, wait_limit_ms: int = 0):
+    h = ctypes.c_void_p()
+    _check(load().sse_server_create(mem_budget_bytes, max_inflight, wait_limit_ms, ctypes.byref(h)),
+           "sse_server_create")
+    return h
+
+
+def sse_submit(server, plan, io: sse_io) -> int:
+    t = ctypes.c_uint64()
+    _check(load().sse_submit(server, plan, ctypes.byref(io), ctypes.byref(t)), "sse_submit")
+    return t.value
+
+
+def sse_poll(server, ticket: int):
+    """(status, sse_result); status is SSE_NOT_READY, SSE_OK or a negative error code
+    (returned, not raised, so callers can inspect failed requests)."""
+    r = sse_result()
+    rc = load().sse_poll(server, ticket, ctypes.byref(r))
+    return rc, r
+
+
+def sse_server_destroy(server) -> None:
+    _check(load().sse_server_destroy(server), "sse_server_destroy")
+
+
+def sse_server_stats(server):
+    rounds, nbytes, n = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32()
+    _check(load().sse_server_stats(server, ctypes.byref(rounds), ctypes.byref(nbytes), ctypes.byref(n)),
+           "sse_server_stats")
+    return rounds.value, nbytes.value, n.value
 
 
 def sse_status_string(status: int) -> str:
