@@ -3,9 +3,10 @@
 // exhaustive autotuner (in the spirit of the tile-size search of Section 3,
 // "Communication Avoidance", which enumerates all feasible tilings).
 //
-// Tuned knobs: tiles per work unit (1 .. 32) and the order in which instances enter the
-// work queue (as given, or longest unit first).  The first call for a batch shape runs
-// every candidate once on the caller's stream and keeps the fastest; the choice is cached
+// Tuned knobs: tiles per work unit (1 .. 16) and the order in which instances enter the
+// work queue (as given, or longest unit first).  The first call for a batch shape times
+// every candidate once on the caller's stream, on a sample of up to 8 instances spread over
+// the size range, and keeps the fastest for the whole batch; the choice is cached
 // in memory and, when SSE_AUTOTUNE_CACHE names a file, appended to that file and read back
 // by later processes.  SSE_AUTOTUNE=0 skips tuning (tiles per unit 2, longest first).
 #include <cuda_runtime.h>
@@ -124,19 +125,39 @@ sse_status run_batch(Plan *const *plans, const double *slots_per_atom, const sse
     sse_status rs = SSE_OK;
     const char *tune_env = getenv("SSE_AUTOTUNE");
     if (!have && allow_tune && !(tune_env && tune_env[0] == '0')) {
-        // exhaustive search: every (tiles per unit, order) candidate, timed once after a warm run
+        // Exhaustive search over (tiles per unit, order), each candidate timed once on a
+        // sample of at most kSample instances spread evenly over the batch sorted by size
+        // (the whole batch when it is that small); one untimed warm run first.
+        constexpr int kSample = 8;
+        std::vector<int> idx(n);
+        for (int i = 0; i < n; ++i) idx[i] = i;
+        std::sort(idx.begin(), idx.end(), [&](int x, int y) {
+            return (long long)plans[x]->d.na * plans[x]->d.ne > (long long)plans[y]->d.na * plans[y]->d.ne;
+        });
+        std::vector<Plan *> sp;
+        std::vector<double> ss;
+        std::vector<sse_io> sio;
+        const int m = n < kSample ? n : kSample;
+        for (int x = 0; x < m; ++x) {
+            const int i = idx[(long long)x * n / m];
+            sp.push_back(plans[i]);
+            ss.push_back(slots_per_atom[i]);
+            sio.push_back(ios[i]);
+        }
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
-        const int tpcs[] = {1, 2, 4, 8, 16, 32};
+        const int tpcs[] = {1, 2, 4, 8, 16};
+        {
+            std::vector<int> order = make_order(sp.data(), ss.data(), m, 2, true);
+            rs = launch_mixed_batch(sp.data(), sio.data(), order.data(), m, 2, queue, st);
+        }
         for (int lpt = 0; lpt < 2 && rs == SSE_OK; ++lpt)
             for (int tpc : tpcs) {
-                std::vector<int> order = make_order(plans, slots_per_atom, n, tpc, lpt != 0);
-                rs = launch_mixed_batch(plans, ios, order.data(), n, tpc, queue, st);
-                if (rs != SSE_OK) break;
+                std::vector<int> order = make_order(sp.data(), ss.data(), m, tpc, lpt != 0);
                 cudaEventRecord(e0, st);
-                rs = launch_mixed_batch(plans, ios, order.data(), n, tpc, queue, st);
+                rs = launch_mixed_batch(sp.data(), sio.data(), order.data(), m, tpc, queue, st);
                 if (rs != SSE_OK) break;
                 cudaEventRecord(e1, st);
                 e = cudaEventSynchronize(e1);

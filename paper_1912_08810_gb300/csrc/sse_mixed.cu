@@ -54,6 +54,15 @@ struct Geo {
     static constexpr int B_PLANE = (kCh / 8) * SBO_B;
     static constexpr int SBO_A = (KST / 8) * 128;
     static constexpr int A_PLANE = (kRowsMax / 8) * SBO_A;
+    // Direct-descriptor form (Nkz = 5): rows (k, j, e) in groups of 8 energies, K per
+    // energy slot = (i, k') padded to 16, Re/Im of X in separate B planes, and the
+    // Toeplitz operand read in place from a per-slot table by shifting the descriptor.
+    static constexpr bool DA = (NK == 5);
+    static constexpr int DA_TE = 8;
+    static constexpr int DA_K = 16;                    // (i, k') per slot, padded
+    static constexpr int DA_SBO_B = (DA_K / 8) * 128;  // 256 bytes
+    static constexpr int DA_B_PLANE = (kCh / 8) * DA_SBO_B;
+    static constexpr int DA_GROUPS = 16;               // 8-row groups of the 128-row tile
 };
 
 constexpr int kMaxInst = 64;  // instances per launch (the descriptors travel as kernel parameters)
@@ -142,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     const int nw = prm.nw;
     const int omega_max = prm.omega_first + nw - 1;
     const int nw0 = nw + GG::P - 1;                   // rows of the table per (k, j)
+    const int da_rows = nw + 2 * GG::DA_TE - 2;       // direct table: rows w0 + (TE - 1), w0 in [1-TE, nw+TE-2]
     constexpr uint32_t tab_stride = GG::KST * 4 + 16;  // hi + lo + 16 bytes against bank conflicts
     // (k, j) groups of rows: padded so that consecutive groups -- read by consecutive lanes --
     // start 16 bytes apart modulo 128 and the 16-byte loads of 8 lanes hit distinct banks
@@ -152,7 +162,9 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     uint8_t *sG = smem + prm.off_g;                 // [2 stages] raw G blocks
     uint8_t *sTab = smem + prm.off_df;                // Toeplitz row table of the current slot
     float2 *sDh = (float2 *)(smem + prm.off_dh);      // [3][144] fp32 dH of the current slot
-    float *sV = (float *)(smem + prm.off_b);          // drained accumulators (overlays B and A)
+    // drained accumulators: overlay B and A, or (direct form) the per-slot table
+    float *sV = (float *)(GG::DA ? smem + prm.off_df : smem + prm.off_b);
+    static_assert(!GG::DA || GG::TE == GG::DA_TE, "direct form expects 8 energies per tile");
     uint64_t *bar_mma = (uint64_t *)(smem + prm.off_bar);
     uint64_t *bar_g = bar_mma + 2;
     uint64_t *bar_job = bar_mma + 4;
@@ -314,6 +326,40 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                 dfold[x] = acc;
             }
             __syncthreads();
+            if constexpr (GG::DA) {
+                // Direct table: [q = Re, Im][hi, lo][group g = (k, j)][K group][row r] x 16 bytes,
+                // entry (i, k') of row r = Re or Im of Df_ij[(k - k') mod Nkz][r - (TE - 1)].
+                const int nitems = 2 * 2 * GG::DA_GROUPS * 2 * da_rows / 2;  // (q, g, kg, r): hi and lo together
+                for (int x = tid; x < nitems; x += kThreads) {
+                    const int r = x % da_rows, kg = (x / da_rows) % 2, g = (x / (2 * da_rows)) % GG::DA_GROUPS;
+                    const int q = x / (2 * da_rows * GG::DA_GROUPS);
+                    const int k = g / 3, j = g % 3, w0 = r - (GG::DA_TE - 1);
+                    float v[8];
+#pragma unroll
+                    for (int xx = 0; xx < 8; ++xx) {
+                        const int kk = kg * 8 + xx;
+                        float val = 0.f;
+                        if (g < 3 * NK && kk < 3 * NK && w0 >= 0 && w0 < nw) {
+                            const int i = kk / NK, kp = kk % NK;
+                            const float2 T = dfold[(((k - kp + NK) % NK) * nw + w0) * 9 + i * 3 + j];
+                            val = q ? T.y : T.x;
+                        }
+                        v[xx] = val;
+                    }
+                    uint32_t hv[4], lv[4];
+#pragma unroll
+                    for (int xx = 0; xx < 4; ++xx) {
+                        const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+                        hv[xx] = hl.x;
+                        lv[xx] = hl.y;
+                    }
+                    const size_t base_hi = ((((size_t)(q * 2 + 0) * GG::DA_GROUPS + g) * 2 + kg) * da_rows + r) * 16;
+                    const size_t base_lo = ((((size_t)(q * 2 + 1) * GG::DA_GROUPS + g) * 2 + kg) * da_rows + r) * 16;
+                    *(uint4 *)(sTab + base_hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    *(uint4 *)(sTab + base_lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                }
+                __syncthreads();
+            } else {
             // Row table of the real-part accumulator's Toeplitz operand: one row per
             // (k, j, w0), w0 in [0, nw0); entry (p, i, k', re/im) = (Re T, -Im T) with
             // T = Df_ij[(k - k') mod Nkz][w0 - p]; bf16 hi plane then lo plane.  A tile row
@@ -349,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                 *(uint4 *)(trow + GG::KST * 2 + gq * 16) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
             }
             __syncthreads();
+            }
         }
 
         // another CTA timed out: stop early instead of waiting out every bound
@@ -400,6 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 
         uint8_t *bhi = sB + sb * (2 * GG::B_PLANE), *blo = bhi + GG::B_PLANE;
         uint8_t *abase = sA + sb * (4 * GG::A_PLANE);
+        uint8_t *bda = sB + sb * (4 * GG::DA_B_PLANE);  // direct form: [re, im][hi, lo] planes
 
         // ---- X slices: X_i[k'][r, t] = sum_u dH_i[r, u] G[k'][u, t] -> B (bf16 hi / lo) ----
         for (int item = tid; item < GG::P * kCh; item += kThreads) {
@@ -437,16 +485,39 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                     lw[i * NK + kp] = hl.y;
                 }
             }
-            const uint32_t row_off = (n >> 3) * GG::SBO_B + (n & 7) * 16 + (p * GG::KS / 8) * 128;
+            if constexpr (GG::DA) {
+                // de-interleave: K index i * Nkz + k' of the Re and Im planes
+                uint32_t hre[8], lre[8], him[8], lim[8];
 #pragma unroll
-            for (int gq = 0; gq < GG::KS / 8; ++gq) {
-                *(uint4 *)(bhi + row_off + gq * 128) = make_uint4(hw[4 * gq], hw[4 * gq + 1], hw[4 * gq + 2], hw[4 * gq + 3]);
-                *(uint4 *)(blo + row_off + gq * 128) = make_uint4(lw[4 * gq], lw[4 * gq + 1], lw[4 * gq + 2], lw[4 * gq + 3]);
+                for (int x = 0; x < 8; ++x) {
+                    const uint32_t h0 = 2 * x < 3 * NK ? hw[2 * x] : 0u, h1 = 2 * x + 1 < 3 * NK ? hw[2 * x + 1] : 0u;
+                    const uint32_t l0 = 2 * x < 3 * NK ? lw[2 * x] : 0u, l1 = 2 * x + 1 < 3 * NK ? lw[2 * x + 1] : 0u;
+                    hre[x] = __byte_perm(h0, h1, 0x5410);
+                    him[x] = __byte_perm(h0, h1, 0x7632);
+                    lre[x] = __byte_perm(l0, l1, 0x5410);
+                    lim[x] = __byte_perm(l0, l1, 0x7632);
+                }
+                const uint32_t row_off = (n >> 3) * GG::DA_SBO_B + (n & 7) * 16;
+#pragma unroll
+                for (int gq = 0; gq < 2; ++gq) {
+                    const uint32_t o = row_off + gq * 128;
+                    *(uint4 *)(bda + 0 * GG::DA_B_PLANE + o) = make_uint4(hre[4 * gq], hre[4 * gq + 1], hre[4 * gq + 2], hre[4 * gq + 3]);
+                    *(uint4 *)(bda + 1 * GG::DA_B_PLANE + o) = make_uint4(lre[4 * gq], lre[4 * gq + 1], lre[4 * gq + 2], lre[4 * gq + 3]);
+                    *(uint4 *)(bda + 2 * GG::DA_B_PLANE + o) = make_uint4(him[4 * gq], him[4 * gq + 1], him[4 * gq + 2], him[4 * gq + 3]);
+                    *(uint4 *)(bda + 3 * GG::DA_B_PLANE + o) = make_uint4(lim[4 * gq], lim[4 * gq + 1], lim[4 * gq + 2], lim[4 * gq + 3]);
+                }
+            } else {
+                const uint32_t row_off = (n >> 3) * GG::SBO_B + (n & 7) * 16 + (p * GG::KS / 8) * 128;
+#pragma unroll
+                for (int gq = 0; gq < GG::KS / 8; ++gq) {
+                    *(uint4 *)(bhi + row_off + gq * 128) = make_uint4(hw[4 * gq], hw[4 * gq + 1], hw[4 * gq + 2], hw[4 * gq + 3]);
+                    *(uint4 *)(blo + row_off + gq * 128) = make_uint4(lw[4 * gq], lw[4 * gq + 1], lw[4 * gq + 2], lw[4 * gq + 3]);
+                }
             }
         }
 
         // ---- Toeplitz slice: A_q[(e, k, j), (p, i, k', re/im)] copied from the row table ----
-        {
+        if constexpr (!GG::DA) {
             uint8_t *ahi = abase + aq * (2 * GG::A_PLANE), *alo = ahi + GG::A_PLANE;
             const uint32_t row_off = (am >> 3) * GG::SBO_A + (am & 7) * 16;
             const int w0 = ae + nw - 1 - GG::P * st;
@@ -480,21 +551,55 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         // ---- MMAs of this stage (one thread) ----
         if (tid == 0) {
             tc_fence_after();
-            constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
-            const uint32_t bh0 = smem_u32(bhi), bl0 = smem_u32(blo);
+            if constexpr (GG::DA) {
+                // A: windows of the direct table starting at row (nw - 1 - st) + (TE - 1)
+                constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
+                constexpr uint32_t idesc_negb = idesc | (1u << 14);
+                const uint32_t lbo_a = (uint32_t)da_rows * 16, sbo_a = 2u * lbo_a;
+                const uint32_t r_start = (uint32_t)(nw - 1 - st + GG::DA_TE - 1);
+                const uint32_t tab0 = smem_u32(sTab) + r_start * 16;
+                const uint32_t tstride = (uint32_t)GG::DA_GROUPS * 2 * da_rows * 16;  // one (q, split) table
+                auto adesc = [&](int q, int split) {
+                    return smem_desc(tab0 + (uint32_t)(q * 2 + split) * tstride, lbo_a, sbo_a);
+                };
+                const uint32_t b0 = smem_u32(bda);
+                auto bdesc = [&](int q, int split) {
+                    return smem_desc(b0 + (uint32_t)(q * 2 + split) * GG::DA_B_PLANE, 128, GG::DA_SBO_B);
+                };
+                const uint64_t are_h = adesc(0, 0), are_l = adesc(0, 1), aim_h = adesc(1, 0), aim_l = adesc(1, 1);
+                const uint64_t bre_h = bdesc(0, 0), bre_l = bdesc(0, 1), bim_h = bdesc(1, 0), bim_l = bdesc(1, 1);
+                const uint32_t dre = tmem, dim = tmem + kAccIm;
+                // Re V = Re T Re X - Im T Im X
+                mma_ss(dre, are_h, bre_h, idesc, job_first ? 0u : 1u);
+                mma_ss(dre, are_h, bre_l, idesc, 1u);
+                mma_ss(dre, are_l, bre_h, idesc, 1u);
+                mma_ss(dre, aim_h, bim_h, idesc_negb, 1u);
+                mma_ss(dre, aim_h, bim_l, idesc_negb, 1u);
+                mma_ss(dre, aim_l, bim_h, idesc_negb, 1u);
+                // Im V = Im T Re X + Re T Im X
+                mma_ss(dim, aim_h, bre_h, idesc, job_first ? 0u : 1u);
+                mma_ss(dim, aim_h, bre_l, idesc, 1u);
+                mma_ss(dim, aim_l, bre_h, idesc, 1u);
+                mma_ss(dim, are_h, bim_h, idesc, 1u);
+                mma_ss(dim, are_h, bim_l, idesc, 1u);
+                mma_ss(dim, are_l, bim_h, idesc, 1u);
+            } else {
+                constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
+                const uint32_t bh0 = smem_u32(bhi), bl0 = smem_u32(blo);
 #pragma unroll
-            for (int ks = 0; ks < GG::KST / 16; ++ks) {
-                const uint64_t bdh = smem_desc(bh0 + ks * 256, 128, GG::SBO_B);
-                const uint64_t bdl = smem_desc(bl0 + ks * 256, 128, GG::SBO_B);
+                for (int ks = 0; ks < GG::KST / 16; ++ks) {
+                    const uint64_t bdh = smem_desc(bh0 + ks * 256, 128, GG::SBO_B);
+                    const uint64_t bdl = smem_desc(bl0 + ks * 256, 128, GG::SBO_B);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const uint32_t ah = smem_u32(abase + q * (2 * GG::A_PLANE)) + ks * 256;
-                    const uint64_t adh = smem_desc(ah, 128, GG::SBO_A);
-                    const uint64_t adl = smem_desc(ah + GG::A_PLANE, 128, GG::SBO_A);
-                    const uint32_t dt = tmem + (q ? kAccIm : 0u);
-                    mma_ss(dt, adh, bdh, idesc, (job_first && ks == 0) ? 0u : 1u);
-                    mma_ss(dt, adh, bdl, idesc, 1u);
-                    mma_ss(dt, adl, bdh, idesc, 1u);
+                    for (int q = 0; q < 2; ++q) {
+                        const uint32_t ah = smem_u32(abase + q * (2 * GG::A_PLANE)) + ks * 256;
+                        const uint64_t adh = smem_desc(ah, 128, GG::SBO_A);
+                        const uint64_t adl = smem_desc(ah + GG::A_PLANE, 128, GG::SBO_A);
+                        const uint32_t dt = tmem + (q ? kAccIm : 0u);
+                        mma_ss(dt, adh, bdh, idesc, (job_first && ks == 0) ? 0u : 1u);
+                        mma_ss(dt, adh, bdl, idesc, 1u);
+                        mma_ss(dt, adl, bdh, idesc, 1u);
+                    }
                 }
             }
             mma_commit(&bar_mma[sb]);
@@ -535,7 +640,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                     for (int s = 0; s < 6; ++s) acc[rl][s] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const int m = pt * 3 + j;
+                    const int m = GG::DA ? (k * 3 + j) * GG::DA_TE + e : pt * 3 + j;
                     const float *vre = sV + m * kVStride, *vim = sV + (kRowsMax + m) * kVStride;
 #pragma unroll
                     for (int tt = 0; tt < 12; ++tt) {
@@ -604,17 +709,31 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
         off += bytes;
         return at;
     };
+    const uint32_t need_v = 2 * kRowsMax * kVStride * 4;
+    const uint32_t dtmp = (uint32_t)(NK * d.nw * 9 * 8);
+    prm.g_stage = (uint32_t)(GG::P * NK * kCh * cbytes);
+    if (GG::DA) {
+        // B stages, raw G, the direct table (the drained accumulators overlay it)
+        const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
+        prm.off_b = take(bsz, 1024);
+        prm.off_a = prm.off_b;
+        prm.off_g = take(2 * prm.g_stage, 128);
+        const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
+        const uint32_t tab = 2u * 2u * GG::DA_GROUPS * 2u * rows * 16u;
+        prm.off_df = take(tab > need_v ? tab : need_v, 1024);
+        prm.off_dh = take(3 * kCh * 8, 16);
+        prm.off_bar = take(64 + 8 + 2 * kMaxSlots * 4, 8);
+        if (dtmp > bsz) return 0xFFFFFFFFu;
+        return off;
+    }
     // B and A stage buffers are contiguous; the drained accumulators and the unrotated
     // Dt table of a job overlay them (never while MMAs read them)
-    const uint32_t need_v = 2 * kRowsMax * kVStride * 4;
     const uint32_t ab = 2 * 2 * GG::B_PLANE + 2 * 4 * GG::A_PLANE;
     prm.off_b = take(ab > need_v ? ab : need_v, 1024);
     prm.off_a = prm.off_b + 2 * 2 * GG::B_PLANE;
-    prm.g_stage = (uint32_t)(GG::P * NK * kCh * cbytes);
     prm.off_g = take(2 * prm.g_stage, 128);
     const uint32_t grp = ((uint32_t)(d.nw + GG::P - 1) * (GG::KST * 4 + 16) + 127u) / 128u * 128u + 16u;
     const uint32_t tab = (uint32_t)(3 * NK) * grp;
-    const uint32_t dtmp = (uint32_t)(NK * d.nw * 9 * 8);
     prm.off_df = take(tab, 16);
     prm.off_dh = take(3 * kCh * 8, 16);
     prm.off_bar = take(64 + 8 + 2 * kMaxSlots * 4, 8);
