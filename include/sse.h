@@ -106,7 +106,12 @@ typedef struct {
 
 /* Validate the geometry (copies neigh to the host once to range-check it: every entry
  * in [-1, na)), choose the kernel and its tiles, and allocate the plan.  On success
- * *out owns a plan that the caller frees with sse_plan_destroy. */
+ * *out owns a plan that the caller frees with sse_plan_destroy.  A mixed-mode plan with
+ * nkz = 5 also owns a workspace of 2 (ne na + 1) x 8 KB (G re-encoded for the tensor-core
+ * product dH_i G, one half per sign), so executions of one plan must not overlap on the GPU:
+ * issue them on one stream or order them with events.  The batched form and the server
+ * keep to this on their own (a plan that appears twice in one batch falls back to the
+ * form without workspace; a server round holds a plan once). */
 SSE_API sse_status sse_plan(const sse_geometry *geo, sse_plan_t **out);
 SSE_API sse_status sse_plan_destroy(sse_plan_t *plan);
 SSE_API sse_status sse_plan_query(const sse_plan_t *plan, sse_plan_info *info);

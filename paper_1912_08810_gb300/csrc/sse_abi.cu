@@ -169,6 +169,7 @@ sse_status sse_plan(const sse_geometry *geo, sse_plan_t **out) {
         p->kernel_id = 1;
         st = mixed_plan_init(*p);
         if (st != SSE_OK) {
+            mixed_plan_free(*p);
             cudaFree(p->d_status);
             delete p;
             return st;

@@ -32,7 +32,8 @@ struct Plan {
     size_t staging_bytes = 0;
     cudaStream_t last_stream = nullptr;
     int64_t workspace_bytes = 0;
-    // Mixed-path workspace (see sse_mixed.cu)
+    // Mixed-path workspace (see sse_mixed.cu): G of each sign re-encoded as bf16 hi/lo
+    // slices in tensor-core operand layout, (ne * na + 1) slices per sign (the last is zero)
     void *mixed_ws = nullptr;
     size_t mixed_ws_bytes = 0;
 };

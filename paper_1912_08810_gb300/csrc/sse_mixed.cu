@@ -38,6 +38,7 @@ constexpr int kRowsMax = 128;    // MMA M
 constexpr int kCh = 144;         // MMA N: channels of a 12 x 12 block
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccIm = 256; // TMEM column of the imaginary accumulator
+constexpr uint32_t kPreCol0 = 192, kPreCol1 = 448;  // pre-product accumulators (64 columns each)
 constexpr uint64_t kWaitNs = 250000000ull;  // bound on every device-side wait (0.25 s)
 constexpr int kMaxSlots = 32;
 constexpr int kVStride = 73;     // row stride (floats) of the drained accumulator tile
@@ -63,7 +64,13 @@ struct Geo {
     static constexpr int DA_SBO_B = (DA_K / 8) * 128;  // 256 bytes
     static constexpr int DA_B_PLANE = (kCh / 8) * DA_SBO_B;
     static constexpr int DA_GROUPS = 16;               // 8-row groups of the 128-row tile
+    // Tensor-core pre-product X = dH . G (with a re-encoded G): rows (i, r, re/im) = 72,
+    // columns (k', t) = 12 Nkz padded to 64, K = (re/im of G, u) = 24 padded to 32.
+    static constexpr int XP_N = 64;
+    static constexpr int XP_SLICE = 8192;              // one (E', f) slice: hi plane + lo plane
+    static constexpr int XP_XS = 61;                   // row stride (floats) of the X transpose buffer
 };
+
 
 constexpr int kMaxInst = 64;  // instances per launch (the descriptors travel as kernel parameters)
 
@@ -81,6 +88,7 @@ struct InstDesc {
     int32_t nchunks;        // units per (sign, atom)
     int32_t nsign;
     long long unit_begin;
+    const uint8_t *gws[2];  // tensor-core form: G re-encoded per sign (see sse_split_g_kernel)
 };
 
 struct MixParams {
@@ -90,7 +98,7 @@ struct MixParams {
     int32_t nst;            // stages per job
     int32_t n_inst;
     long long total_units;
-    uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, g_stage;
+    uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, off_x, g_stage;
     InstDesc inst[kMaxInst];
 };
 
@@ -119,6 +127,40 @@ __device__ __forceinline__ uint4 to_im_pairs(uint4 v) {
     return make_uint4(to_im_pair(v.x), to_im_pair(v.y), to_im_pair(v.z), to_im_pair(v.w));
 }
 
+// G of one sign re-encoded for the tensor-core pre-product: slice (E', f) holds, for rows
+// n' = k' * 12 + t (12 Nkz used, 64 rows) and K = pc * 12 + u (24 used, 32), the bf16 hi
+// plane then the lo plane of the pc-part of G[k', E', f][u, t], in the K-major core-matrix
+// layout (SBO 512, LBO 128).  One CTA per slice.
+template <typename CT>
+__global__ void __launch_bounds__(256) sse_split_g_kernel(const CT *__restrict__ G, uint8_t *__restrict__ ws,
+                                                          int ne, int na, int nkz) {
+    const long long slice = blockIdx.x;
+    const int E = (int)(slice / na), f = (int)(slice % na);
+    const int np = threadIdx.x >> 2, kg = threadIdx.x & 3;
+    float v[8];
+#pragma unroll
+    for (int xx = 0; xx < 8; ++xx) {
+        const int kk = kg * 8 + xx;
+        float val = 0.f;
+        if (np < nkz * 12 && kk < 24) {
+            const int kp = np / 12, t = np % 12, pc = kk / 12, u = kk % 12;
+            const float2 c = load_c32(G + (((size_t)kp * ne + E) * na + f) * kCh + u * 12 + t);
+            val = pc ? c.y : c.x;
+        }
+        v[xx] = val;
+    }
+    uint32_t hv[4], lv[4];
+#pragma unroll
+    for (int xx = 0; xx < 4; ++xx) {
+        const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+        hv[xx] = hl.x;
+        lv[xx] = hl.y;
+    }
+    uint8_t *dst = ws + slice * 8192 + (np >> 3) * 512 + kg * 128 + (np & 7) * 16;
+    *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    *(uint4 *)(dst + 4096) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+}
+
 template <typename CT>
 __device__ __forceinline__ void rmw_store(CT *dst, float2 v, bool first);
 template <>
@@ -143,9 +185,10 @@ __device__ __forceinline__ void rmw_store<float2>(float2 *dst, float2 v, bool fi
     *dst = make_float2(f64_to_f32(x), f64_to_f32(y));
 }
 
-template <int NK, typename CT>
+template <int NK, typename CT, bool V3>
 __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_constant__ MixParams prm) {
     using GG = Geo<NK>;
+    static_assert(!V3 || GG::DA, "the tensor-core pre-product runs with the direct Toeplitz form");
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nw = prm.nw;
@@ -166,13 +209,17 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     float *sV = (float *)(GG::DA ? smem + prm.off_df : smem + prm.off_b);
     static_assert(!GG::DA || GG::TE == GG::DA_TE, "direct form expects 8 energies per tile");
     uint64_t *bar_mma = (uint64_t *)(smem + prm.off_bar);
-    uint64_t *bar_g = bar_mma + 2;
-    uint64_t *bar_job = bar_mma + 4;
-    uint64_t *bar_fin = bar_mma + 5;                 // only for draining MMAs on abort
-    uint32_t *s_tmem = (uint32_t *)(bar_mma + 6);
+    uint64_t *bar_g = bar_mma + 2;                   // [3] (two used without the pre-product)
+    uint64_t *bar_job = bar_mma + 5;
+    uint64_t *bar_fin = bar_mma + 6;                 // only for draining MMAs on abort
+    uint64_t *bar_pre = bar_mma + 7;                 // [2] pre-product MMAs done
+    uint32_t *s_tmem = (uint32_t *)(bar_mma + 9);
     int *s_abort = (int *)(s_tmem + 1);
     int *s_nvalid = s_abort + 1;
-    long long *s_unit = (long long *)(smem + prm.off_bar + 64);
+    long long *s_unit = (long long *)(smem + prm.off_bar + 128);
+    uint8_t *sPreB = smem + prm.off_g;                // pre-product: [3] G slices (TMA)
+    uint8_t *sApre = smem + prm.off_a;                // pre-product: dH operand [hi, lo]
+    float *sX = (float *)(smem + prm.off_x);          // pre-product: X rows (i, r, re/im) x (k', t)
     int *s_slot = (int *)(s_unit + 1);                // [kMaxSlots] valid slot indices
     int *s_f = s_slot + kMaxSlots;                    // [kMaxSlots] their neighbour atoms
 
@@ -181,8 +228,11 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         mbar_init(&bar_mma[1], 1);
         mbar_init(&bar_g[0], 1);
         mbar_init(&bar_g[1], 1);
+        mbar_init(&bar_g[2], 1);
         mbar_init(bar_job, 1);
         mbar_init(bar_fin, 1);
+        mbar_init(&bar_pre[0], 1);
+        mbar_init(&bar_pre[1], 1);
         fence_mbar_init();
         *s_abort = 0;
     }
@@ -196,6 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     const uint32_t tmem = *s_tmem;
 
     // Per-thread A-builder row: thread -> (accumulator q, row m).
+    int last_g[3] = {-1, -1, -1};  // thread 0: last stage whose G slice went to each buffer
     const int aq = tid >> 7, am = tid & 127;
     const bool arow_ok = am < GG::ROWS;
     const int ae = am / (3 * NK), ak = (am / 3) % NK, aj = am % 3;
@@ -296,7 +347,45 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         }
     };
 
-    if (tid == 0 && total > 0) issue_g(0);
+    // Thread 0: bulk-copy the re-encoded G slice of stage g (one 8 KB copy; the zero slice
+    // stands in for energies below or above the grid) into pre-product buffer gg % 3.
+    auto issue_pre = [&](int g) {
+        int t, vs, st;
+        decode(g, t, vs, st);
+        const int f = s_f[vs];
+        const int Ep = t * GG::TE - omega_max + st;
+        const long long slice = (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + f : (long long)d.ne * d.na;
+        const int gg = g_base + g;
+        uint64_t *bar = &bar_g[gg % 3];
+        mbar_arrive_expect_tx(bar, GG::XP_SLICE);
+        bulk_g2s(sPreB + (gg % 3) * GG::XP_SLICE, I.gws[sign] + slice * GG::XP_SLICE, GG::XP_SLICE, bar);
+        last_g[gg % 3] = gg;
+    };
+    // Thread 0: pre-product MMAs of stage g into D_pre[gg & 1] once its G slice is in.
+    auto issue_premma = [&](int g) -> bool {
+        const int gg = g_base + g;
+        if (!mbar_wait_bounded(&bar_g[gg % 3], (gg / 3) & 1, kWaitNs)) return false;
+        tc_fence_after();
+        constexpr uint32_t idesc_x = idesc_bf16_f32(kRowsMax, GG::XP_N);
+        const uint32_t a0 = smem_u32(sApre), b0 = smem_u32(sPreB + (gg % 3) * GG::XP_SLICE);
+        const uint32_t dx = tmem + ((gg & 1) ? kPreCol1 : kPreCol0);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ah = smem_desc(a0 + ks * 256, 128, 512), al = smem_desc(a0 + 8192 + ks * 256, 128, 512);
+            const uint64_t bh = smem_desc(b0 + ks * 256, 128, 512), bl = smem_desc(b0 + 4096 + ks * 256, 128, 512);
+            mma_ss(dx, ah, bh, idesc_x, ks ? 1u : 0u);
+            mma_ss(dx, ah, bl, idesc_x, 1u);
+            mma_ss(dx, al, bh, idesc_x, 1u);
+        }
+        mma_commit(&bar_pre[gg & 1]);
+        return true;
+    };
+    if constexpr (V3) {
+        if (tid == 0 && total > 0) issue_pre(0);
+        if (tid == 0 && total > 1) issue_pre(1);
+    } else {
+        if (tid == 0 && total > 0) issue_g(0);
+    }
 
     for (int g = 0; g < total && !abort; ++g) {
         int t, vs, st;
@@ -358,7 +447,43 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                     *(uint4 *)(sTab + base_hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                     *(uint4 *)(sTab + base_lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                 }
+                if constexpr (V3) {
+                    // pre-product operand A_pre[(i, r, re/im), (pc, u)]: the complex product
+                    // dH_i . G as a real one (rows pr = re: (Re dH, -Im dH); pr = im: (Im dH, Re dH))
+                    for (int x = tid; x < kRowsMax * 4; x += kThreads) {
+                        const int m = x >> 2, kg = x & 3;
+                        float v[8];
+#pragma unroll
+                        for (int xx = 0; xx < 8; ++xx) {
+                            const int kk = kg * 8 + xx;
+                            float val = 0.f;
+                            if (m < 72 && kk < 24) {
+                                const int pr = m & 1, r = (m >> 1) % 12, i = (m >> 1) / 12, pc = kk / 12, u = kk % 12;
+                                const float2 h = sDh[i * kCh + r * 12 + u];
+                                val = pr ? (pc ? h.x : h.y) : (pc ? -h.y : h.x);
+                            }
+                            v[xx] = val;
+                        }
+                        uint32_t hv[4], lv[4];
+#pragma unroll
+                        for (int xx = 0; xx < 4; ++xx) {
+                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+                            hv[xx] = hl.x;
+                            lv[xx] = hl.y;
+                        }
+                        uint8_t *dst = sApre + (m >> 3) * 512 + kg * 128 + (m & 7) * 16;
+                        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *(uint4 *)(dst + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    }
+                    fence_proxy_async_smem();
+                }
                 __syncthreads();
+                if constexpr (V3) {
+                    if (tid == 0 && !issue_premma(g)) {
+                        *s_abort = 1;
+                        atomicExch(prm.status, 1);
+                    }
+                }
             } else {
             // Row table of the real-part accumulator's Toeplitz operand: one row per
             // (k, j, w0), w0 in [0, nw0); entry (p, i, k', re/im) = (Re T, -Im T) with
@@ -400,6 +525,17 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 
         // another CTA timed out: stop early instead of waiting out every bound
         if (tid == 0 && *(volatile int32_t *)prm.status != 0) *s_abort = 1;
+        uint8_t *gbuf = sG + sb * prm.g_stage;
+        float2 *g32 = (float2 *)gbuf;  // [p][k'][u][t] complex fp32
+        if constexpr (V3) {
+            if (tid == 0 && g + 2 < total) issue_pre(g + 2);
+            // X of this stage: its pre-product MMAs were issued one stage earlier
+            if (!mbar_wait_bounded(&bar_pre[gg & 1], (gg >> 1) & 1, kWaitNs)) {
+                *s_abort = 1;
+                atomicExch(prm.status, 1);
+            }
+            tc_fence_after();
+        } else {
         if (tid == 0 && g + 1 < total) issue_g(g + 1);
 
         // ---- G blocks of this stage: wait, convert to fp32 in place, zero the gaps ----
@@ -407,8 +543,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             *s_abort = 1;
             atomicExch(prm.status, 1);
         }
-        uint8_t *gbuf = sG + sb * prm.g_stage;
-        float2 *g32 = (float2 *)gbuf;  // [p][k'][u][t] complex fp32
         {
             constexpr int NE_ = GG::P * NK * kCh;
             constexpr int PER = (NE_ + kThreads - 1) / kThreads;
@@ -437,6 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                 if (x < NE_) g32[x] = v[r];
             }
         }
+        }  // !V3
 
         // ---- the stage buffers must be free: MMAs of stage g - 2 complete ----
         if (gg >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((gg >> 1) - 1) & 1, kWaitNs)) {
@@ -449,8 +584,63 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         uint8_t *abase = sA + sb * (4 * GG::A_PLANE);
         uint8_t *bda = sB + sb * (4 * GG::DA_B_PLANE);  // direct form: [re, im][hi, lo] planes
 
+        if constexpr (V3) {
+            // ---- X from the pre-product accumulator: TMEM rows (i, r, re/im) -> sX ----
+            if (warp < 3) {
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + ((gg & 1) ? kPreCol1 : kPreCol0);
+                const int m = warp * 32 + lane;
+#pragma unroll
+                for (int c0 = 0; c0 < GG::XP_N; c0 += 8) {
+                    float v[8];
+                    tmem_ld8(taddr + c0, v);
+                    tmem_ld_wait();
+                    if (m < 72) {
+#pragma unroll
+                        for (int x = 0; x < 8; ++x)
+                            if (c0 + x < NK * 12) sX[m * GG::XP_XS + c0 + x] = v[x];
+                    }
+                }
+                tc_fence_before();
+            }
+            __syncthreads();
+            // ---- X -> B planes [re, im][hi, lo] of channel n = (r, t), K index i * Nkz + k' ----
+            if (tid < kCh) {
+                const int n = tid, r = n / 12, tt = n % 12;
+                float xre[16], xim[16];
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) {
+                    xre[kk] = 0.f;
+                    xim[kk] = 0.f;
+                    if (kk < 3 * NK) {
+                        const int i = kk / NK, kp = kk % NK;
+                        const float *row = sX + ((i * 12 + r) * 2) * GG::XP_XS + kp * 12 + tt;
+                        xre[kk] = row[0];
+                        xim[kk] = row[GG::XP_XS];
+                    }
+                }
+                uint32_t hre[8], lre[8], him[8], lim[8];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const uint2 a = split2_bf16(xre[2 * x], xre[2 * x + 1]);
+                    const uint2 b = split2_bf16(xim[2 * x], xim[2 * x + 1]);
+                    hre[x] = a.x;
+                    lre[x] = a.y;
+                    him[x] = b.x;
+                    lim[x] = b.y;
+                }
+                const uint32_t row_off = (n >> 3) * GG::DA_SBO_B + (n & 7) * 16;
+#pragma unroll
+                for (int gq = 0; gq < 2; ++gq) {
+                    const uint32_t o = row_off + gq * 128;
+                    *(uint4 *)(bda + 0 * GG::DA_B_PLANE + o) = make_uint4(hre[4 * gq], hre[4 * gq + 1], hre[4 * gq + 2], hre[4 * gq + 3]);
+                    *(uint4 *)(bda + 1 * GG::DA_B_PLANE + o) = make_uint4(lre[4 * gq], lre[4 * gq + 1], lre[4 * gq + 2], lre[4 * gq + 3]);
+                    *(uint4 *)(bda + 2 * GG::DA_B_PLANE + o) = make_uint4(him[4 * gq], him[4 * gq + 1], him[4 * gq + 2], him[4 * gq + 3]);
+                    *(uint4 *)(bda + 3 * GG::DA_B_PLANE + o) = make_uint4(lim[4 * gq], lim[4 * gq + 1], lim[4 * gq + 2], lim[4 * gq + 3]);
+                }
+            }
+        }
         // ---- X slices: X_i[k'][r, t] = sum_u dH_i[r, u] G[k'][u, t] -> B (bf16 hi / lo) ----
-        for (int item = tid; item < GG::P * kCh; item += kThreads) {
+        for (int item = tid; item < (V3 ? 0 : GG::P * kCh); item += kThreads) {
             const int p = item / kCh, n = item % kCh, r = n / 12, tt = n % 12;
             uint32_t hw[GG::KS / 2], lw[GG::KS / 2];
 #pragma unroll
@@ -551,6 +741,13 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         // ---- MMAs of this stage (one thread) ----
         if (tid == 0) {
             tc_fence_after();
+            if constexpr (V3) {
+                // the next stage's pre-product first, so its X is ready while these MMAs run
+                if (!job_last && g + 1 < total && !issue_premma(g + 1)) {
+                    *s_abort = 1;
+                    atomicExch(prm.status, 1);
+                }
+            }
             if constexpr (GG::DA) {
                 // A: windows of the direct table starting at row (nw - 1 - st) + (TE - 1)
                 constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
@@ -690,9 +887,15 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         if (tid == 0) mma_commit(bar_fin);  // arrives once every MMA issued so far is done
         mbar_wait_bounded(bar_fin, 0, kWaitNs);
         // the bulk copies of the aborted stage and of the one prefetched after it
-        if (abort_g >= 0) mbar_wait_bounded(&bar_g[abort_g & 1], (abort_g >> 1) & 1, kWaitNs);
-        if (abort_g + 1 < abort_total)
-            mbar_wait_bounded(&bar_g[(abort_g + 1) & 1], ((abort_g + 1) >> 1) & 1, kWaitNs);
+        if constexpr (V3) {
+            if (tid == 0)
+                for (int b = 0; b < 3; ++b)
+                    if (last_g[b] >= 0) mbar_wait_bounded(&bar_g[b], (last_g[b] / 3) & 1, kWaitNs);
+        } else {
+            if (abort_g >= 0) mbar_wait_bounded(&bar_g[abort_g & 1], (abort_g >> 1) & 1, kWaitNs);
+            if (abort_g + 1 < abort_total)
+                mbar_wait_bounded(&bar_g[(abort_g + 1) & 1], ((abort_g + 1) >> 1) & 1, kWaitNs);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -700,7 +903,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 }
 
 template <int NK>
-uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
+uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm, bool v3) {
     using GG = Geo<NK>;
     uint32_t off = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
@@ -713,16 +916,24 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
     const uint32_t dtmp = (uint32_t)(NK * d.nw * 9 * 8);
     prm.g_stage = (uint32_t)(GG::P * NK * kCh * cbytes);
     if (GG::DA) {
-        // B stages, raw G, the direct table (the drained accumulators overlay it)
+        // B stages, raw G (or the pre-product's G slices and dH operand and X buffer), the
+        // direct table (the drained accumulators overlay it)
         const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
         prm.off_b = take(bsz, 1024);
-        prm.off_a = prm.off_b;
-        prm.off_g = take(2 * prm.g_stage, 128);
+        if (v3) {
+            prm.off_g = take(3 * GG::XP_SLICE, 1024);
+            prm.off_a = take(2 * 8192, 1024);
+            prm.off_x = take(72 * GG::XP_XS * 4, 16);
+        } else {
+            prm.off_a = prm.off_b;
+            prm.off_g = take(2 * prm.g_stage, 128);
+            prm.off_x = 0;
+        }
         const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
         const uint32_t tab = 2u * 2u * GG::DA_GROUPS * 2u * rows * 16u;
         prm.off_df = take(tab > need_v ? tab : need_v, 1024);
         prm.off_dh = take(3 * kCh * 8, 16);
-        prm.off_bar = take(64 + 8 + 2 * kMaxSlots * 4, 8);
+        prm.off_bar = take(128 + 8 + 2 * kMaxSlots * 4, 8);
         if (dtmp > bsz) return 0xFFFFFFFFu;
         return off;
     }
@@ -736,7 +947,8 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
     const uint32_t tab = (uint32_t)(3 * NK) * grp;
     prm.off_df = take(tab, 16);
     prm.off_dh = take(3 * kCh * 8, 16);
-    prm.off_bar = take(64 + 8 + 2 * kMaxSlots * 4, 8);
+    prm.off_bar = take(128 + 8 + 2 * kMaxSlots * 4, 8);
+    prm.off_x = 0;
     if (dtmp > (ab > need_v ? ab : need_v)) return 0xFFFFFFFFu;
     return off;
 }
@@ -763,16 +975,20 @@ bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc) {
     I.nqz = p.d.nqz;
     I.ntiles = (I.ne + GG::TE - 1) / GG::TE;
     I.tiles_per_cta = tpc < 1 ? 1 : (tpc > I.ntiles ? I.ntiles : tpc);
+    const size_t sign_bytes = ((size_t)p.d.ne * p.d.na + 1) * 8192;
+    const uint8_t *ws = (const uint8_t *)p.mixed_ws;
+    I.gws[0] = ws ? ws + (do_gt ? 0 : sign_bytes) : nullptr;
+    I.gws[1] = ws ? ws + sign_bytes : nullptr;
     I.nchunks = (I.ntiles + I.tiles_per_cta - 1) / I.tiles_per_cta;
     return true;
 }
 
 long long inst_units(const InstDesc &I) { return (long long)I.nsign * I.na * I.nchunks; }
 
-template <int NK, typename CT>
+template <int NK, typename CT, bool V3>
 sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *status) {
     using GG = Geo<NK>;
-    smem = mixed_smem_bytes<NK>(d, sizeof(CT), prm);
+    smem = mixed_smem_bytes<NK>(d, sizeof(CT), prm, V3);
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
         return SSE_E_INVALID_ARG;
@@ -782,9 +998,26 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
     prm.nw = d.nw;
     prm.omega_first = d.omega_first;
     prm.nst = (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
-    cudaError_t e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT, V3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed kernel)");
+    return SSE_OK;
+}
+
+// Re-encode the G of every requested sign of one instance into its plan's workspace.
+template <typename CT>
+sse_status split_g(const Plan &p, const sse_io &io, cudaStream_t st) {
+    const size_t sign_bytes = ((size_t)p.d.ne * p.d.na + 1) * 8192;
+    const void *gs[2] = {io.S_gt ? io.G_gt : nullptr, io.S_lt ? io.G_lt : nullptr};
+    for (int s = 0; s < 2; ++s) {
+        if (!gs[s]) continue;
+        const long long slices = (long long)p.d.ne * p.d.na;
+        if (slices > 0x7fffffffLL) return set_error("mixed mode: too many G slices"), SSE_E_INVALID_ARG;
+        sse_split_g_kernel<CT><<<(unsigned)slices, 256, 0, st>>>((const CT *)gs[s], (uint8_t *)p.mixed_ws + s * sign_bytes,
+                                                                p.d.ne, p.d.na, p.d.nkz);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch sse_split_g_kernel");
     return SSE_OK;
 }
 
@@ -792,12 +1025,12 @@ bool aligned16(const sse_io &io) {
     return ((((uintptr_t)io.G_gt | (uintptr_t)io.G_lt)) & 15u) == 0;
 }
 
-template <int NK, typename CT>
+template <int NK, typename CT, bool V3>
 sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     using GG = Geo<NK>;
     MixParams prm{};
     uint32_t smem = 0;
-    sse_status rs = prepare<NK, CT>(prm, smem, p.d, p.d_status);
+    sse_status rs = prepare<NK, CT, V3>(prm, smem, p.d, p.d_status);
     if (rs != SSE_OK) return rs;
     if (!aligned16(io)) return set_error("mixed mode: G buffers must be 16-byte aligned"), SSE_E_INVALID_ARG;
     // tiles per unit: enough units for several waves over the SMs
@@ -813,7 +1046,11 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     prm.total_units = inst_units(prm.inst[0]);
     prm.queue = nullptr;
     if (prm.total_units > 0x7fffffffLL) return set_error("mixed mode: grid too large"), SSE_E_INVALID_ARG;
-    sse_mixed_kernel<NK, CT><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
+    if (V3) {
+        rs = split_g<CT>(p, io, st);
+        if (rs != SSE_OK) return rs;
+    }
+    sse_mixed_kernel<NK, CT, V3><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch sse_mixed_kernel");
     p.tile_e = GG::TE;
@@ -821,7 +1058,7 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
 }
 
 // Persistent launches over many instances: one CTA per SM pulls units from a counter.
-template <int NK, typename CT>
+template <int NK, typename CT, bool V3>
 sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
                            int32_t *queue, cudaStream_t st) {
     int sms = 148;
@@ -829,7 +1066,7 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
     for (int base = 0; base < n; base += kMaxInst) {
         MixParams prm{};
         uint32_t smem = 0;
-        sse_status rs = prepare<NK, CT>(prm, smem, plans[order[base]]->d, plans[order[base]]->d_status);
+        sse_status rs = prepare<NK, CT, V3>(prm, smem, plans[order[base]]->d, plans[order[base]]->d_status);
         if (rs != SSE_OK) return rs;
         long long units = 0;
         int m = 0;
@@ -838,6 +1075,10 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
             const sse_io &io = ios[order[x]];
             if (!aligned16(io)) return set_error("mixed mode: G buffers must be 16-byte aligned"), SSE_E_INVALID_ARG;
             if (!fill_inst<NK>(prm.inst[m], p, io, tpc)) continue;
+            if (V3) {
+                rs = split_g<CT>(p, io, st);
+                if (rs != SSE_OK) return rs;
+            }
             prm.inst[m].unit_begin = units;
             units += inst_units(prm.inst[m]);
             ++m;
@@ -849,7 +1090,7 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return cuda_fail(e, "reset the work counter");
         const long long grid = units < sms ? units : sms;
-        sse_mixed_kernel<NK, CT><<<(unsigned)grid, kThreads, smem, st>>>(prm);
+        sse_mixed_kernel<NK, CT, V3><<<(unsigned)grid, kThreads, smem, st>>>(prm);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "launch persistent sse_mixed_kernel");
     }
@@ -859,11 +1100,11 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
 template <typename CT>
 sse_status launch_dtype(Plan &p, const sse_io &io, cudaStream_t st) {
     switch (p.d.nkz) {
-        case 1: return launch_nk<1, CT>(p, io, st);
-        case 2: return launch_nk<2, CT>(p, io, st);
-        case 3: return launch_nk<3, CT>(p, io, st);
-        case 4: return launch_nk<4, CT>(p, io, st);
-        case 5: return launch_nk<5, CT>(p, io, st);
+        case 1: return launch_nk<1, CT, false>(p, io, st);
+        case 2: return launch_nk<2, CT, false>(p, io, st);
+        case 3: return launch_nk<3, CT, false>(p, io, st);
+        case 4: return launch_nk<4, CT, false>(p, io, st);
+        case 5: return p.mixed_ws ? launch_nk<5, CT, true>(p, io, st) : launch_nk<5, CT, false>(p, io, st);
         default:
             set_error("mixed mode supports Nkz <= 5 (got %d)", p.d.nkz);
             return SSE_E_INVALID_ARG;
@@ -874,11 +1115,20 @@ template <typename CT>
 sse_status launch_batch_dtype(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
                               int32_t *queue, cudaStream_t st) {
     switch (plans[order[0]]->d.nkz) {
-        case 1: return launch_batch_nk<1, CT>(plans, ios, order, n, tpc, queue, st);
-        case 2: return launch_batch_nk<2, CT>(plans, ios, order, n, tpc, queue, st);
-        case 3: return launch_batch_nk<3, CT>(plans, ios, order, n, tpc, queue, st);
-        case 4: return launch_batch_nk<4, CT>(plans, ios, order, n, tpc, queue, st);
-        case 5: return launch_batch_nk<5, CT>(plans, ios, order, n, tpc, queue, st);
+        case 1: return launch_batch_nk<1, CT, false>(plans, ios, order, n, tpc, queue, st);
+        case 2: return launch_batch_nk<2, CT, false>(plans, ios, order, n, tpc, queue, st);
+        case 3: return launch_batch_nk<3, CT, false>(plans, ios, order, n, tpc, queue, st);
+        case 4: return launch_batch_nk<4, CT, false>(plans, ios, order, n, tpc, queue, st);
+        case 5: {
+            // the pre-product form needs each plan's workspace for itself: every plan once
+            bool all_ws = true;
+            for (int x = 0; x < n && all_ws; ++x) {
+                all_ws = plans[order[x]]->mixed_ws != nullptr;
+                for (int y = 0; y < x && all_ws; ++y) all_ws = plans[order[y]] != plans[order[x]];
+            }
+            return all_ws ? launch_batch_nk<5, CT, true>(plans, ios, order, n, tpc, queue, st)
+                          : launch_batch_nk<5, CT, false>(plans, ios, order, n, tpc, queue, st);
+        }
         default:
             set_error("mixed mode supports Nkz <= 5");
             return SSE_E_INVALID_ARG;
@@ -906,20 +1156,41 @@ sse_status mixed_plan_init(Plan &p) {
     uint32_t smem = 0;
     const size_t cb = elem_bytes(p.geo.dtype);
     switch (d.nkz) {
-        case 1: smem = mixed_smem_bytes<1>(d, cb, prm); p.tile_e = tile_e_of<1>(); break;
-        case 2: smem = mixed_smem_bytes<2>(d, cb, prm); p.tile_e = tile_e_of<2>(); break;
-        case 3: smem = mixed_smem_bytes<3>(d, cb, prm); p.tile_e = tile_e_of<3>(); break;
-        case 4: smem = mixed_smem_bytes<4>(d, cb, prm); p.tile_e = tile_e_of<4>(); break;
-        default: smem = mixed_smem_bytes<5>(d, cb, prm); p.tile_e = tile_e_of<5>(); break;
+        case 1: smem = mixed_smem_bytes<1>(d, cb, prm, false); p.tile_e = tile_e_of<1>(); break;
+        case 2: smem = mixed_smem_bytes<2>(d, cb, prm, false); p.tile_e = tile_e_of<2>(); break;
+        case 3: smem = mixed_smem_bytes<3>(d, cb, prm, false); p.tile_e = tile_e_of<3>(); break;
+        case 4: smem = mixed_smem_bytes<4>(d, cb, prm, false); p.tile_e = tile_e_of<4>(); break;
+        default: smem = mixed_smem_bytes<5>(d, cb, prm, true); p.tile_e = tile_e_of<5>(); break;
     }
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
         return SSE_E_INVALID_ARG;
     }
+    if (d.nkz == 5) {
+        // workspace of the tensor-core pre-product: G re-encoded per sign, plus a zero slice
+        const size_t sign_bytes = ((size_t)d.ne * d.na + 1) * 8192;
+        cudaError_t e = cudaMalloc(&p.mixed_ws, 2 * sign_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p.mixed_ws = nullptr;
+            set_error("cudaMalloc of %zu bytes for the mixed workspace failed", 2 * sign_bytes);
+            return SSE_E_OUT_OF_MEMORY;
+        }
+        p.mixed_ws_bytes = 2 * sign_bytes;
+        p.workspace_bytes += (int64_t)p.mixed_ws_bytes;
+        for (int s2 = 0; s2 < 2; ++s2) {
+            e = cudaMemset((uint8_t *)p.mixed_ws + s2 * sign_bytes + (size_t)d.ne * d.na * 8192, 0, 8192);
+            if (e != cudaSuccess) return cuda_fail(e, "clear the zero slice");
+        }
+    }
     return SSE_OK;
 }
 
-void mixed_plan_free(Plan &p) { (void)p; }
+void mixed_plan_free(Plan &p) {
+    if (p.mixed_ws) cudaFree(p.mixed_ws);
+    p.mixed_ws = nullptr;
+    p.mixed_ws_bytes = 0;
+}
 
 sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st) {
     if (p.geo.dtype == SSE_C128) return launch_dtype<double2>(p, io, st);

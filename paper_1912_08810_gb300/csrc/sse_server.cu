@@ -182,16 +182,24 @@ void server_loop(sse_server_s *s) {
                 s->inflight_bytes += q.bytes;
                 s->pending.pop_front();
             }
-            // one round per compatible group of admitted requests, at most two rounds queued
+            // one round per compatible group of admitted requests, at most two rounds queued;
+            // a plan runs in one round at a time and once per round (its workspace is its own)
             while (s->running.size() < 2) {
                 std::vector<uint64_t> group;
+                std::vector<const sse_plan_t *> busy;
+                for (const Round &r : s->running)
+                    for (uint64_t tk : r.tickets) busy.push_back(s->reqs[tk].plan);
                 const Plan *ref = nullptr;
                 for (auto &kv : s->reqs) {
                     Request &q = kv.second;
                     if (q.state != kAdmitted) continue;
+                    if (std::find(busy.begin(), busy.end(), q.plan) != busy.end()) continue;
                     const Plan *p = plan_core(q.plan);
                     if (!ref) ref = p;
-                    if (compatible(*ref, *p)) group.push_back(kv.first);
+                    if (compatible(*ref, *p)) {
+                        group.push_back(kv.first);
+                        busy.push_back(q.plan);
+                    }
                 }
                 if (group.empty()) break;
                 std::sort(group.begin(), group.end());  // arrival order
