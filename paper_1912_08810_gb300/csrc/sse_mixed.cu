@@ -161,28 +161,25 @@ __global__ void __launch_bounds__(256) sse_split_g_kernel(const CT *__restrict__
     *(uint4 *)(dst + 4096) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
 }
 
+// Sigma after one more slot: the slot's FP32 contribution v added in FP64 to the value
+// stored so far (old), or v alone for the first slot.
 template <typename CT>
-__device__ __forceinline__ void rmw_store(CT *dst, float2 v, bool first);
+__device__ __forceinline__ CT slot_sum(float2 v, CT old, bool first);
 template <>
-__device__ __forceinline__ void rmw_store<double2>(double2 *dst, float2 v, bool first) {
+__device__ __forceinline__ double2 slot_sum<double2>(float2 v, double2 old, bool first) {
     double2 o = make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
     if (!first) {
-        const double2 old = *dst;
         o.x += old.x;
         o.y += old.y;
     }
-    *dst = o;
+    return o;
 }
 template <>
-__device__ __forceinline__ void rmw_store<float2>(float2 *dst, float2 v, bool first) {
-    if (first) {
-        *dst = v;
-        return;
-    }
-    const float2 old = *dst;
+__device__ __forceinline__ float2 slot_sum<float2>(float2 v, float2 old, bool first) {
+    if (first) return v;
     const double x = f32_to_f64(old.x) + f32_to_f64(v.x);
     const double y = f32_to_f64(old.y) + f32_to_f64(v.y);
-    *dst = make_float2(f64_to_f32(x), f64_to_f32(y));
+    return make_float2(f64_to_f32(x), f64_to_f32(y));
 }
 
 template <int NK, typename CT, bool V3>
@@ -205,8 +202,18 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     uint8_t *sG = smem + prm.off_g;                 // [2 stages] raw G blocks
     uint8_t *sTab = smem + prm.off_df;                // Toeplitz row table of the current slot
     float2 *sDh = (float2 *)(smem + prm.off_dh);      // [3][144] fp32 dH of the current slot
-    // drained accumulators: overlay B and A, or (direct form) the per-slot table
-    float *sV = (float *)(GG::DA ? smem + prm.off_df : smem + prm.off_b);
+    // Jobs (tile, slot) of a unit run slot-major, so the per-slot tables are built once per
+    // slot and reused by the unit's tiles; the direct form without the pre-product keeps
+    // tile-major order because its drained accumulators overlay the direct table.
+    constexpr bool SLOT_OUTER = V3 || !GG::DA;
+    // epilogue: the accumulators are drained in EP_PARTS column blocks of EP_R rows r
+    constexpr int EP_PARTS = V3 ? 3 : 2;
+    constexpr int EP_COLS = kCh / EP_PARTS, EP_STRIDE = EP_COLS + 1, EP_R = EP_COLS / 12;
+    constexpr int EP_RB = EP_R / 2, EP_NSB = 6 / EP_RB, EP_S = 12 / EP_NSB;
+    static_assert(EP_STRIDE * 2 * kRowsMax * 4 <= 2 * kRowsMax * kVStride * 4, "drain buffer");
+    // drained accumulators: overlay B and A; the direct form: the per-slot table, or with the
+    // pre-product the B stages and the X buffer
+    float *sV = (float *)(V3 ? smem + prm.off_b : GG::DA ? smem + prm.off_df : smem + prm.off_b);
     static_assert(!GG::DA || GG::TE == GG::DA_TE, "direct form expects 8 energies per tile");
     uint64_t *bar_mma = (uint64_t *)(smem + prm.off_bar);
     uint64_t *bar_g = bar_mma + 2;                   // [3] (two used without the pre-product)
@@ -253,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 
     bool abort = false;
     int abort_g = -1, abort_total = 0;
-    int g_base = 0, job_base = 0;  // stages and jobs this CTA ran before the current unit
+    int g_base = 0;   // stages this CTA ran before the current unit
+    int job_ctr = 0;  // jobs this CTA completed (phase of the job barrier)
     for (long long iter = 0;; ++iter) {
     // ---- next unit: one per CTA, or pulled from the work counter ----
     __syncthreads();
@@ -314,17 +322,29 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             }
     }
 
-    // Decode a global stage index into (tile, valid-slot index, stage within the job).
-    auto decode = [&](int g, int &t, int &vs, int &st) {
-        const int job = g / prm.nst;
-        st = g - job * prm.nst;
-        t = t_begin + job / nvalid;
-        vs = job % nvalid;
-    };
-    // Thread 0: bulk-copy the G blocks of stage g into raw buffer g % 2.
-    auto issue_g = [&](int g) {
+    // Position of a stage in the unit: (tile, valid-slot index, stage within the job),
+    // stepped forward without divisions.
+    struct Pos {
         int t, vs, st;
-        decode(g, t, vs, st);
+    };
+    auto advance = [&](Pos &p) {
+        if (++p.st < prm.nst) return;
+        p.st = 0;
+        if constexpr (SLOT_OUTER) {
+            if (++p.t == t_end) {
+                p.t = t_begin;
+                ++p.vs;
+            }
+        } else {
+            if (++p.vs == nvalid) {
+                p.vs = 0;
+                ++p.t;
+            }
+        }
+    };
+    // Thread 0: bulk-copy the G blocks of stage g (at position q) into raw buffer g % 2.
+    auto issue_g = [&](int g, const Pos &q) {
+        const int t = q.t, vs = q.vs, st = q.st;
         const int f = s_f[vs];
         const int e_first = t * GG::TE - omega_max + GG::P * st;
         uint32_t bytes = 0;
@@ -349,9 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 
     // Thread 0: bulk-copy the re-encoded G slice of stage g (one 8 KB copy; the zero slice
     // stands in for energies below or above the grid) into pre-product buffer gg % 3.
-    auto issue_pre = [&](int g) {
-        int t, vs, st;
-        decode(g, t, vs, st);
+    auto issue_pre = [&](int g, const Pos &q) {
+        const int t = q.t, vs = q.vs, st = q.st;
         const int f = s_f[vs];
         const int Ep = t * GG::TE - omega_max + st;
         const long long slice = (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + f : (long long)d.ne * d.na;
@@ -380,25 +399,30 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         mma_commit(&bar_pre[gg & 1]);
         return true;
     };
+    Pos cur{t_begin, 0, 0};  // the stage being built
+    Pos pf{t_begin, 0, 0};   // thread 0: the next stage to prefetch
     if constexpr (V3) {
-        if (tid == 0 && total > 0) issue_pre(0);
-        if (tid == 0 && total > 1) issue_pre(1);
+        if (tid == 0 && total > 0) issue_pre(0, pf), advance(pf);
+        if (tid == 0 && total > 1) issue_pre(1, pf), advance(pf);
     } else {
-        if (tid == 0 && total > 0) issue_g(0);
+        if (tid == 0 && total > 0) issue_g(0, pf), advance(pf);
     }
 
-    for (int g = 0; g < total && !abort; ++g) {
-        int t, vs, st;
-        decode(g, t, vs, st);
+    for (int g = 0; g < total && !abort; ++g, advance(cur)) {
+        const int t = cur.t, vs = cur.vs, st = cur.st;
         const int gg = g_base + g;  // CTA-wide stage index: buffer and barrier phases
         const int sb = gg & 1;
         const int E0 = t * GG::TE;
-        const int job = job_base + g / prm.nst;
         const bool job_first = st == 0, job_last = st == prm.nst - 1;
+        // first stage of a slot's first job / last stage of a slot's last job
+        const bool slot_first = job_first && (!SLOT_OUTER || t == t_begin);
+        const bool slot_last = job_last && (!SLOT_OUTER || t + 1 == t_end);
 
-        if (job_first) {
-            // Slot tables for this job: dH (fp32) and the folded, split, k-rotated Dt.
-            // The previous job's MMAs are complete, so the A/B area is free scratch.
+        // another CTA timed out: stop early instead of waiting out every bound
+        if (job_first && tid == 0 && *(volatile int32_t *)prm.status != 0) *s_abort = 1;
+        if (slot_first) {
+            // Slot tables: dH (fp32) and the folded, split, k-rotated Dt.  The previous
+            // job's MMAs are complete, so the B (and A) stages are free scratch.
             const int b = s_slot[vs];
             const CT *dh = dH + ((size_t)a * d.nb + b) * 3 * kCh;
             for (int x = tid; x < 3 * kCh; x += kThreads) sDh[x] = load_c32(dh + x);
@@ -523,12 +547,10 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             }
         }
 
-        // another CTA timed out: stop early instead of waiting out every bound
-        if (tid == 0 && *(volatile int32_t *)prm.status != 0) *s_abort = 1;
         uint8_t *gbuf = sG + sb * prm.g_stage;
         float2 *g32 = (float2 *)gbuf;  // [p][k'][u][t] complex fp32
         if constexpr (V3) {
-            if (tid == 0 && g + 2 < total) issue_pre(g + 2);
+            if (tid == 0 && g + 2 < total) issue_pre(g + 2, pf), advance(pf);
             // X of this stage: its pre-product MMAs were issued one stage earlier
             if (!mbar_wait_bounded(&bar_pre[gg & 1], (gg >> 1) & 1, kWaitNs)) {
                 *s_abort = 1;
@@ -536,7 +558,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             }
             tc_fence_after();
         } else {
-        if (tid == 0 && g + 1 < total) issue_g(g + 1);
+        if (tid == 0 && g + 1 < total) issue_g(g + 1, pf), advance(pf);
 
         // ---- G blocks of this stage: wait, convert to fp32 in place, zero the gaps ----
         if (!mbar_wait_bounded(&bar_g[sb], (gg >> 1) & 1, kWaitNs)) {
@@ -589,53 +611,45 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             if (warp < 3) {
                 const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + ((gg & 1) ? kPreCol1 : kPreCol0);
                 const int m = warp * 32 + lane;
+                uint32_t x0[32], x1[32];
+                tmem_ld32(taddr, x0);
+                tmem_ld32(taddr + 32, x1);
+                tmem_ld_wait();
+                if (m < 72) {
+                    float *row = sX + m * GG::XP_XS;
 #pragma unroll
-                for (int c0 = 0; c0 < GG::XP_N; c0 += 8) {
-                    float v[8];
-                    tmem_ld8(taddr + c0, v);
-                    tmem_ld_wait();
-                    if (m < 72) {
+                    for (int x = 0; x < 32; ++x) row[x] = __uint_as_float(x0[x]);
 #pragma unroll
-                        for (int x = 0; x < 8; ++x)
-                            if (c0 + x < NK * 12) sX[m * GG::XP_XS + c0 + x] = v[x];
-                    }
+                    for (int x = 0; x < NK * 12 - 32; ++x) row[32 + x] = __uint_as_float(x1[x]);
                 }
                 tc_fence_before();
             }
             __syncthreads();
             // ---- X -> B planes [re, im][hi, lo] of channel n = (r, t), K index i * Nkz + k' ----
-            if (tid < kCh) {
-                const int n = tid, r = n / 12, tt = n % 12;
-                float xre[16], xim[16];
+            for (int item = tid; item < 2 * kCh; item += kThreads) {
+                const int n = item % kCh, pr = item / kCh, r = n / 12, tt = n % 12;
+                float xv[16];
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) {
-                    xre[kk] = 0.f;
-                    xim[kk] = 0.f;
+                    xv[kk] = 0.f;
                     if (kk < 3 * NK) {
                         const int i = kk / NK, kp = kk % NK;
-                        const float *row = sX + ((i * 12 + r) * 2) * GG::XP_XS + kp * 12 + tt;
-                        xre[kk] = row[0];
-                        xim[kk] = row[GG::XP_XS];
+                        xv[kk] = sX[((i * 12 + r) * 2 + pr) * GG::XP_XS + kp * 12 + tt];
                     }
                 }
-                uint32_t hre[8], lre[8], him[8], lim[8];
+                uint32_t hv[8], lv[8];
 #pragma unroll
                 for (int x = 0; x < 8; ++x) {
-                    const uint2 a = split2_bf16(xre[2 * x], xre[2 * x + 1]);
-                    const uint2 b = split2_bf16(xim[2 * x], xim[2 * x + 1]);
-                    hre[x] = a.x;
-                    lre[x] = a.y;
-                    him[x] = b.x;
-                    lim[x] = b.y;
+                    const uint2 hl = split2_bf16(xv[2 * x], xv[2 * x + 1]);
+                    hv[x] = hl.x;
+                    lv[x] = hl.y;
                 }
                 const uint32_t row_off = (n >> 3) * GG::DA_SBO_B + (n & 7) * 16;
+                uint8_t *ph = bda + (2 * pr) * GG::DA_B_PLANE, *pl = ph + GG::DA_B_PLANE;
 #pragma unroll
                 for (int gq = 0; gq < 2; ++gq) {
-                    const uint32_t o = row_off + gq * 128;
-                    *(uint4 *)(bda + 0 * GG::DA_B_PLANE + o) = make_uint4(hre[4 * gq], hre[4 * gq + 1], hre[4 * gq + 2], hre[4 * gq + 3]);
-                    *(uint4 *)(bda + 1 * GG::DA_B_PLANE + o) = make_uint4(lre[4 * gq], lre[4 * gq + 1], lre[4 * gq + 2], lre[4 * gq + 3]);
-                    *(uint4 *)(bda + 2 * GG::DA_B_PLANE + o) = make_uint4(him[4 * gq], him[4 * gq + 1], him[4 * gq + 2], him[4 * gq + 3]);
-                    *(uint4 *)(bda + 3 * GG::DA_B_PLANE + o) = make_uint4(lim[4 * gq], lim[4 * gq + 1], lim[4 * gq + 2], lim[4 * gq + 3]);
+                    *(uint4 *)(ph + row_off + gq * 128) = make_uint4(hv[4 * gq], hv[4 * gq + 1], hv[4 * gq + 2], hv[4 * gq + 3]);
+                    *(uint4 *)(pl + row_off + gq * 128) = make_uint4(lv[4 * gq], lv[4 * gq + 1], lv[4 * gq + 2], lv[4 * gq + 3]);
                 }
             }
         }
@@ -743,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             tc_fence_after();
             if constexpr (V3) {
                 // the next stage's pre-product first, so its X is ready while these MMAs run
-                if (!job_last && g + 1 < total && !issue_premma(g + 1)) {
+                if (!slot_last && g + 1 < total && !issue_premma(g + 1)) {
                     *s_abort = 1;
                     atomicExch(prm.status, 1);
                 }
@@ -806,19 +820,37 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         if (!job_last) continue;
 
         // ---- epilogue of the job: V = acc_re + i acc_im, Sigma += sum_j V_j dH_j^+ ----
-        if (!mbar_wait_bounded(bar_job, job & 1, kWaitNs)) {
+        if (!mbar_wait_bounded(bar_job, job_ctr & 1, kWaitNs)) {
             *s_abort = 1;
             atomicExch(prm.status, 1);
         }
         tc_fence_after();
+        ++job_ctr;
         const bool first_slot = vs == 0;
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < EP_PARTS; ++h) {
+            // the slots summed so far, fetched before the drain so their latency overlaps it
+            const int ep_pt = tid / 6, ep_rb = (tid % 6) / EP_NSB, ep_sbk = (tid % 6) % EP_NSB;
+            const int ep_e = ep_pt / NK, ep_k = ep_pt % NK, ep_E = E0 + ep_e;
+            const bool ep_live = tid < NK * GG::TE * 6 && ep_E < d.ne;
+            CT *ep_dst[2];
+            CT old[2][EP_S];
+#pragma unroll
+            for (int rl = 0; rl < 2; ++rl) {
+                const int r = EP_R * h + 2 * ep_rb + rl;
+                ep_dst[rl] = S + (((size_t)ep_k * d.ne + (ep_live ? ep_E : 0)) * d.na + a) * kCh + r * 12 + EP_S * ep_sbk;
+#pragma unroll
+                for (int s = 0; s < EP_S; ++s) {
+                    old[rl][s].x = 0;
+                    old[rl][s].y = 0;
+                    if (ep_live && !first_slot) old[rl][s] = ep_dst[rl][s];
+                }
+            }
             {
                 const int qd = warp & 3, q = warp >> 2;
-                const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (q ? kAccIm : 0u) + 72 * h;
-                float *vrow = sV + (q * kRowsMax + qd * 32 + lane) * kVStride;
+                const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (q ? kAccIm : 0u) + EP_COLS * h;
+                float *vrow = sV + (q * kRowsMax + qd * 32 + lane) * EP_STRIDE;
 #pragma unroll
-                for (int c0 = 0; c0 < 72; c0 += 8) {
+                for (int c0 = 0; c0 < EP_COLS; c0 += 8) {
                     float v[8];
                     tmem_ld8(taddr + c0, v);
                     tmem_ld_wait();
@@ -828,17 +860,17 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             }
             __syncthreads();
             if (tid < NK * GG::TE * 6) {
-                const int pt = tid / 6, rb = (tid % 6) >> 1, sbk = tid & 1;
-                const int e = pt / NK, k = pt % NK;
-                float2 acc[2][6];
+                const int pt = ep_pt, rb = ep_rb, sbk = ep_sbk;
+                const int e = ep_e, k = ep_k;
+                float2 acc[2][EP_S];
 #pragma unroll
                 for (int rl = 0; rl < 2; ++rl)
 #pragma unroll
-                    for (int s = 0; s < 6; ++s) acc[rl][s] = make_float2(0.f, 0.f);
+                    for (int s = 0; s < EP_S; ++s) acc[rl][s] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const int m = GG::DA ? (k * 3 + j) * GG::DA_TE + e : pt * 3 + j;
-                    const float *vre = sV + m * kVStride, *vim = sV + (kRowsMax + m) * kVStride;
+                    const float *vre = sV + m * EP_STRIDE, *vim = sV + (kRowsMax + m) * EP_STRIDE;
 #pragma unroll
                     for (int tt = 0; tt < 12; ++tt) {
                         float2 vv[2];
@@ -848,22 +880,18 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                             vv[rl] = make_float2(vre[col], vim[col]);
                         }
 #pragma unroll
-                        for (int s = 0; s < 6; ++s) {
-                            const float2 hv = sDh[j * kCh + (6 * sbk + s) * 12 + tt];
+                        for (int s = 0; s < EP_S; ++s) {
+                            const float2 hv = sDh[j * kCh + (EP_S * sbk + s) * 12 + tt];
 #pragma unroll
                             for (int rl = 0; rl < 2; ++rl) acc[rl][s] = cmul_conj_acc(acc[rl][s], vv[rl], hv);
                         }
                     }
                 }
-                const int E = E0 + e;
-                if (E < d.ne) {
+                if (ep_live) {
 #pragma unroll
-                    for (int rl = 0; rl < 2; ++rl) {
-                        const int r = 6 * h + 2 * rb + rl;
-                        CT *dst = S + (((size_t)k * d.ne + E) * d.na + a) * kCh + r * 12 + 6 * sbk;
+                    for (int rl = 0; rl < 2; ++rl)
 #pragma unroll
-                        for (int s = 0; s < 6; ++s) rmw_store<CT>(dst + s, acc[rl][s], first_slot);
-                    }
+                        for (int s = 0; s < EP_S; ++s) ep_dst[rl][s] = slot_sum<CT>(acc[rl][s], old[rl][s], first_slot);
                 }
             }
             __syncthreads();
@@ -878,7 +906,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         }
     }
     g_base += total;
-    job_base += njobs;
     if (abort) break;
     }  // units
 
@@ -902,6 +929,536 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---- the tensor-core form with the pre-product (Nkz = 5), warp-specialised ---------------
+//
+// Same arithmetic as the direct form above with X = dH_i . G taken from the tensor cores,
+// but the CTA is split by role so that the MMAs of one stage run while the next stage is
+// prepared: eight builder warps (slot tables, X drain, B operand, epilogue) and one control
+// warp whose lane 0 issues the bulk copies of the G slices and every MMA.  Hand-offs go
+// through mbarriers: builders -> control "B of stage g ready" and "slot tables ready";
+// control -> builders through MMA commits ("X of stage g ready", "job accumulated").
+// In-order completion of one thread's MMAs gives the rest: the commit of stage g's
+// pre-product is issued after stage g-2's main MMAs, so its arrival also frees that
+// stage's B buffer, and the G-slice ring slot it used two stages later.
+constexpr int kTcBuilders = 256;
+constexpr int kTcThreads = kTcBuilders + 32;
+constexpr int kTcRing = 4;   // G slices in flight
+constexpr int kDhJ = 160;    // float2 per direction j of the padded dH copy
+
+// dH_j[s, t] in shared memory: rows s in blocks of 4 with 4 float2 of padding between
+// blocks, so the epilogue's three row blocks read distinct banks.
+__device__ __forceinline__ int dh_at(int j, int s, int t) { return j * kDhJ + s * 12 + t + (s >> 2) * 4; }
+__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+template <typename CT>
+__global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_constant__ MixParams prm) {
+    constexpr int NK = 5;
+    using GG = Geo<NK>;
+    constexpr int EP_PARTS = 3, EP_COLS = kCh / EP_PARTS, EP_STRIDE = EP_COLS + 1, EP_R = EP_COLS / 12;
+    constexpr int EP_NSB = 3, EP_S = 12 / EP_NSB;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool ctl = warp == kTcBuilders / 32;
+    const int nw = prm.nw;
+    const int omega_max = prm.omega_first + nw - 1;
+    const int da_rows = nw + 2 * GG::DA_TE - 2;
+
+    uint8_t *sB = smem + prm.off_b;              // [2 stages][re hi, re lo, im hi, im lo]
+    float *sX = (float *)(smem + prm.off_x);     // X rows (i, r, re/im) x (k', t)
+    float *sV = (float *)(smem + prm.off_b);     // epilogue: overlays the B stages and X
+    uint8_t *sRing = smem + prm.off_g;           // [kTcRing] re-encoded G slices
+    uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
+    uint8_t *sTab = smem + prm.off_df;           // direct Toeplitz table of the slot
+    float2 *sDh = (float2 *)(smem + prm.off_dh);
+    uint64_t *bars = (uint64_t *)(smem + prm.off_bar);
+    uint64_t *bar_g = bars;                      // [kTcRing] slice landed
+    uint64_t *bar_pre = bars + kTcRing;          // [2] pre-product of a stage done
+    uint64_t *bar_bready = bars + kTcRing + 2;   // [2] B of a stage built
+    uint64_t *bar_job = bars + kTcRing + 4;      // last MMAs of a job done
+    uint64_t *bar_slot = bars + kTcRing + 5;     // slot tables built
+    uint64_t *bar_fin = bars + kTcRing + 6;      // abort: every MMA issued so far done
+    uint32_t *s_tmem = (uint32_t *)(bars + kTcRing + 7);
+    // abort flags: builders write slot g & 1 during stage g and all read it after the stage's
+    // last barrier (the next write to that slot comes after another barrier); the control
+    // warp has its own flag
+    int *s_abort = (int *)(s_tmem + 1);          // [2]
+    int *s_abort_ctl = s_abort + 2;
+    int *s_nvalid = s_abort + 3;
+    long long *s_unit = (long long *)(smem + prm.off_bar + 128);
+    int *s_slot = (int *)(s_unit + 1);
+    int *s_f = s_slot + kMaxSlots;
+
+    if (tid == 0) {
+        for (int b = 0; b < kTcRing; ++b) mbar_init(&bar_g[b], 1);
+        mbar_init(&bar_pre[0], 1);
+        mbar_init(&bar_pre[1], 1);
+        mbar_init(&bar_bready[0], kTcBuilders);
+        mbar_init(&bar_bready[1], kTcBuilders);
+        mbar_init(bar_job, 1);
+        mbar_init(bar_slot, kTcBuilders);
+        mbar_init(bar_fin, 1);
+        fence_mbar_init();
+        s_abort[0] = 0;
+        s_abort[1] = 0;
+        *s_abort_ctl = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(s_tmem, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    int last_g[kTcRing];  // control lane 0: last stage copied into each ring slot
+#pragma unroll
+    for (int b = 0; b < kTcRing; ++b) last_g[b] = -1;
+    int g_base = 0, job_ctr = 0, slot_ctr = 0;
+    bool abort = false;
+    for (long long iter = 0;; ++iter) {
+        __syncthreads();
+        if (tid == 0) {
+            long long u;
+            if (prm.queue) u = atomicAdd(prm.queue, 1);
+            else u = iter == 0 ? (long long)blockIdx.x : prm.total_units;
+            if (*(volatile int32_t *)prm.status != 0) u = prm.total_units;
+            *s_unit = u;
+        }
+        __syncthreads();
+        const long long unit = *s_unit;
+        if (unit >= prm.total_units) break;
+        int ii = 0;
+        while (ii + 1 < prm.n_inst && prm.inst[ii + 1].unit_begin <= unit) ++ii;
+        const InstDesc &I = prm.inst[ii];
+        const long long local = unit - I.unit_begin;
+        const int sign = (int)(local / ((long long)I.na * I.nchunks));
+        const long long rem = local - (long long)sign * I.na * I.nchunks;
+        const int a = (int)(rem / I.nchunks), chunk = (int)(rem % I.nchunks);
+        const Dims d{prm.nkz, I.nqz, I.ne, nw, I.na, I.nb, prm.omega_first};
+        const CT *__restrict__ D = (const CT *)I.D[sign];
+        CT *__restrict__ S = (CT *)I.S[sign];
+        const CT *__restrict__ dH = (const CT *)I.dH;
+        const int t_begin = chunk * I.tiles_per_cta;
+        const int t_end = min(I.ntiles, t_begin + I.tiles_per_cta);
+        if (tid == 0) {
+            int nv = 0;
+            for (int b = 0; b < d.nb && nv < kMaxSlots; ++b) {
+                const int f = __ldg(I.neigh + (size_t)a * d.nb + b);
+                if (f >= 0) {
+                    s_slot[nv] = b;
+                    s_f[nv] = f;
+                    ++nv;
+                }
+            }
+            *s_nvalid = nv;
+        }
+        __syncthreads();
+        const int nvalid = *s_nvalid;
+        const int total = (t_end - t_begin) * nvalid * prm.nst;
+        if (nvalid == 0) {
+            for (int t = t_begin; t < t_end; ++t)
+                for (int x = tid; x < NK * GG::TE * kCh; x += kTcThreads) {
+                    const int e = x / (NK * kCh), k = (x / kCh) % NK, c = x % kCh;
+                    const int E = t * GG::TE + e;
+                    if (E < d.ne) {
+                        CT z;
+                        z.x = 0;
+                        z.y = 0;
+                        S[(((size_t)k * d.ne + E) * d.na + a) * kCh + c] = z;
+                    }
+                }
+        }
+        // stage position (tile, valid-slot index, stage within the job), slot-major
+        struct Pos {
+            int t, vs, st;
+        };
+        auto advance = [&](Pos &p) {
+            if (++p.st < prm.nst) return;
+            p.st = 0;
+            if (++p.t == t_end) {
+                p.t = t_begin;
+                ++p.vs;
+            }
+        };
+
+        if (ctl) {
+            // ================= control warp: bulk copies and MMAs (lane 0) =================
+            if (lane == 0) {
+                auto issue_pre = [&](int g, const Pos &q) {
+                    const int f = s_f[q.vs];
+                    const int Ep = q.t * GG::TE - omega_max + q.st;
+                    const long long slice =
+                        (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + f : (long long)d.ne * d.na;
+                    const int gg = g_base + g;
+                    uint64_t *bar = &bar_g[gg % kTcRing];
+                    mbar_arrive_expect_tx(bar, GG::XP_SLICE);
+                    bulk_g2s(sRing + (gg % kTcRing) * GG::XP_SLICE, I.gws[sign] + slice * GG::XP_SLICE,
+                             GG::XP_SLICE, bar);
+                    last_g[gg % kTcRing] = gg;
+                };
+                auto premma = [&](int g) -> bool {
+                    const int gg = g_base + g;
+                    if (!mbar_wait_bounded(&bar_g[gg % kTcRing], (gg / kTcRing) & 1, kWaitNs)) return false;
+                    tc_fence_after();
+                    constexpr uint32_t idesc_x = idesc_bf16_f32(kRowsMax, GG::XP_N);
+                    const uint32_t a0 = smem_u32(sApre), b0 = smem_u32(sRing + (gg % kTcRing) * GG::XP_SLICE);
+                    const uint32_t dx = tmem + ((gg & 1) ? kPreCol1 : kPreCol0);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ah = smem_desc(a0 + ks * 256, 128, 512), al = smem_desc(a0 + 8192 + ks * 256, 128, 512);
+                        const uint64_t bh = smem_desc(b0 + ks * 256, 128, 512), bl = smem_desc(b0 + 4096 + ks * 256, 128, 512);
+                        mma_ss(dx, ah, bh, idesc_x, ks ? 1u : 0u);
+                        mma_ss(dx, ah, bl, idesc_x, 1u);
+                        mma_ss(dx, al, bh, idesc_x, 1u);
+                    }
+                    mma_commit(&bar_pre[gg & 1]);
+                    return true;
+                };
+                Pos m{t_begin, 0, 0}, pf{t_begin, 0, 0};
+                for (int x = 0; x < kTcRing - 1 && x < total; ++x) {
+                    issue_pre(x, pf);
+                    advance(pf);
+                }
+                constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
+                constexpr uint32_t idesc_negb = idesc | (1u << 14);
+                const uint32_t lbo_a = (uint32_t)da_rows * 16, sbo_a = 2u * lbo_a;
+                const uint32_t tstride = (uint32_t)GG::DA_GROUPS * 2 * da_rows * 16;
+                bool ok = true;
+                for (int g = 0; g < total; ++g, advance(m)) {
+                    const int gg = g_base + g;
+                    const bool job_first = m.st == 0, job_last = m.st == prm.nst - 1;
+                    const bool slot_first = job_first && m.t == t_begin;
+                    const bool slot_last = job_last && m.t + 1 == t_end;
+                    if (slot_first) {
+                        ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs);
+                        ++slot_ctr;
+                        if (!ok) break;
+                        tc_fence_after();
+                        if (!(ok = premma(g))) break;
+                    }
+                    if (!(ok = mbar_wait_bounded(&bar_bready[gg & 1], (gg >> 1) & 1, kWaitNs))) break;
+                    tc_fence_after();
+                    if (g + kTcRing - 1 < total) {
+                        issue_pre(g + kTcRing - 1, pf);
+                        advance(pf);
+                    }
+                    // the next stage's pre-product first, so its X is ready while these MMAs run
+                    if (!slot_last && g + 1 < total && !(ok = premma(g + 1))) break;
+                    // A: windows of the direct table starting at row (nw - 1 - st) + (TE - 1)
+                    const uint32_t r_start = (uint32_t)(nw - 1 - m.st + GG::DA_TE - 1);
+                    const uint32_t tab0 = smem_u32(sTab) + r_start * 16;
+                    auto adesc = [&](int q, int split) {
+                        return smem_desc(tab0 + (uint32_t)(q * 2 + split) * tstride, lbo_a, sbo_a);
+                    };
+                    const uint32_t b0 = smem_u32(sB + (gg & 1) * (4 * GG::DA_B_PLANE));
+                    auto bdesc = [&](int q, int split) {
+                        return smem_desc(b0 + (uint32_t)(q * 2 + split) * GG::DA_B_PLANE, 128, GG::DA_SBO_B);
+                    };
+                    const uint64_t are_h = adesc(0, 0), are_l = adesc(0, 1), aim_h = adesc(1, 0), aim_l = adesc(1, 1);
+                    const uint64_t bre_h = bdesc(0, 0), bre_l = bdesc(0, 1), bim_h = bdesc(1, 0), bim_l = bdesc(1, 1);
+                    const uint32_t dre = tmem, dim = tmem + kAccIm;
+                    const uint32_t acc0 = job_first ? 0u : 1u;
+                    // Re V = Re T Re X - Im T Im X
+                    mma_ss(dre, are_h, bre_h, idesc, acc0);
+                    mma_ss(dre, are_h, bre_l, idesc, 1u);
+                    mma_ss(dre, are_l, bre_h, idesc, 1u);
+                    mma_ss(dre, aim_h, bim_h, idesc_negb, 1u);
+                    mma_ss(dre, aim_h, bim_l, idesc_negb, 1u);
+                    mma_ss(dre, aim_l, bim_h, idesc_negb, 1u);
+                    // Im V = Im T Re X + Re T Im X
+                    mma_ss(dim, aim_h, bre_h, idesc, acc0);
+                    mma_ss(dim, aim_h, bre_l, idesc, 1u);
+                    mma_ss(dim, aim_l, bre_h, idesc, 1u);
+                    mma_ss(dim, are_h, bim_h, idesc, 1u);
+                    mma_ss(dim, are_h, bim_l, idesc, 1u);
+                    mma_ss(dim, are_l, bim_h, idesc, 1u);
+                    if (job_last) mma_commit(bar_job);
+                }
+                if (!ok) {
+                    *s_abort_ctl = 1;
+                    atomicExch(prm.status, 1);
+                }
+            }
+            __syncwarp();
+        } else {
+            // ================= builder warps =================
+            Pos cur{t_begin, 0, 0};
+            for (int g = 0; g < total; ++g, advance(cur)) {
+                const int t = cur.t, vs = cur.vs, st = cur.st;
+                const int gg = g_base + g, sb = gg & 1;
+                const int E0 = t * GG::TE;
+                const bool job_first = st == 0, job_last = st == prm.nst - 1;
+                const bool slot_first = job_first && t == t_begin;
+                // another CTA timed out: stop early instead of waiting out every bound
+                if (job_first && tid == 0 && *(volatile int32_t *)prm.status != 0) s_abort[sb] = 1;
+
+                if (slot_first) {
+                    // Slot tables: dH (fp32, padded), the direct Toeplitz table of the folded,
+                    // split, k-rotated Dt, and the pre-product's dH operand.  No MMA reads
+                    // them now: the previous job's MMAs are complete.
+                    const int b = s_slot[vs];
+                    const CT *dh = dH + ((size_t)a * d.nb + b) * 3 * kCh;
+                    for (int x = tid; x < 3 * kCh; x += kTcBuilders)
+                        sDh[dh_at(x / kCh, (x % kCh) / 12, x % 12)] = load_c32(dh + x);
+                    float2 *dfold = (float2 *)sB;  // [kappa][w][ij] folded Dt, B stages as scratch
+                    for (int x = tid; x < NK * nw * 9; x += kTcBuilders) {
+                        const int ij = x % 9, w = (x / 9) % nw, kap = x / (9 * nw);
+                        float2 acc = make_float2(0.f, 0.f);
+                        for (int q = kap; q < d.nqz; q += NK) {
+                            const float2 v = load_c32(D + ((((size_t)q * nw + w) * d.na + a) * d.nb + b) * 9 + ij);
+                            acc.x += v.x;
+                            acc.y += v.y;
+                        }
+                        dfold[x] = acc;
+                    }
+                    builders_sync();
+                    const int nitems = 2 * 2 * GG::DA_GROUPS * 2 * da_rows / 2;
+                    for (int x = tid; x < nitems; x += kTcBuilders) {
+                        const int r = x % da_rows, kg = (x / da_rows) % 2, gq = (x / (2 * da_rows)) % GG::DA_GROUPS;
+                        const int q = x / (2 * da_rows * GG::DA_GROUPS);
+                        const int k = gq / 3, j = gq % 3, w0 = r - (GG::DA_TE - 1);
+                        float v[8];
+#pragma unroll
+                        for (int xx = 0; xx < 8; ++xx) {
+                            const int kk = kg * 8 + xx;
+                            float val = 0.f;
+                            if (gq < 3 * NK && kk < 3 * NK && w0 >= 0 && w0 < nw) {
+                                const int i = kk / NK, kp = kk % NK;
+                                const float2 T = dfold[(((k - kp + NK) % NK) * nw + w0) * 9 + i * 3 + j];
+                                val = q ? T.y : T.x;
+                            }
+                            v[xx] = val;
+                        }
+                        uint32_t hv[4], lv[4];
+#pragma unroll
+                        for (int xx = 0; xx < 4; ++xx) {
+                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+                            hv[xx] = hl.x;
+                            lv[xx] = hl.y;
+                        }
+                        const size_t base_hi = ((((size_t)(q * 2 + 0) * GG::DA_GROUPS + gq) * 2 + kg) * da_rows + r) * 16;
+                        const size_t base_lo = ((((size_t)(q * 2 + 1) * GG::DA_GROUPS + gq) * 2 + kg) * da_rows + r) * 16;
+                        *(uint4 *)(sTab + base_hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *(uint4 *)(sTab + base_lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    }
+                    // A_pre[(i, r, re/im), (pc, u)]: the complex product dH_i . G as a real one
+                    // (row re: (Re dH, -Im dH); row im: (Im dH, Re dH))
+                    for (int x = tid; x < kRowsMax * 4; x += kTcBuilders) {
+                        const int m = x >> 2, kg = x & 3;
+                        float v[8];
+#pragma unroll
+                        for (int xx = 0; xx < 8; ++xx) {
+                            const int kk = kg * 8 + xx;
+                            float val = 0.f;
+                            if (m < 72 && kk < 24) {
+                                const int pr = m & 1, r = (m >> 1) % 12, i = (m >> 1) / 12, pc = kk / 12, u = kk % 12;
+                                const float2 h = sDh[dh_at(i, r, u)];
+                                val = pr ? (pc ? h.x : h.y) : (pc ? -h.y : h.x);
+                            }
+                            v[xx] = val;
+                        }
+                        uint32_t hv[4], lv[4];
+#pragma unroll
+                        for (int xx = 0; xx < 4; ++xx) {
+                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+                            hv[xx] = hl.x;
+                            lv[xx] = hl.y;
+                        }
+                        uint8_t *dst = sApre + (m >> 3) * 512 + kg * 128 + (m & 7) * 16;
+                        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *(uint4 *)(dst + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    }
+                    fence_proxy_async_smem();
+                    mbar_arrive(bar_slot);
+                }
+
+                // ---- X of this stage: TMEM rows (i, r, re/im) -> sX ----
+                if (!mbar_wait_bounded(&bar_pre[sb], (gg >> 1) & 1, kWaitNs)) {
+                    s_abort[sb] = 1;
+                    atomicExch(prm.status, 1);
+                }
+                tc_fence_after();
+                if ((warp & 3) < 3) {
+                    const int half = warp >> 2;  // columns 0..31 or 32..59
+                    const uint32_t taddr =
+                        tmem + ((uint32_t)((warp & 3) * 32) << 16) + (sb ? kPreCol1 : kPreCol0) + 32 * half;
+                    const int m = (warp & 3) * 32 + lane;
+                    uint32_t xr[32];
+                    tmem_ld32(taddr, xr);
+                    tmem_ld_wait();
+                    if (m < 72) {
+                        float *row = sX + m * GG::XP_XS + 32 * half;
+                        const int ncol = half ? NK * 12 - 32 : 32;
+#pragma unroll
+                        for (int x = 0; x < 32; ++x)
+                            if (x < ncol) row[x] = __uint_as_float(xr[x]);
+                    }
+                    tc_fence_before();
+                }
+                builders_sync();
+                // ---- X -> B planes [re, im][hi, lo] of channel n = (r, t), K index i * Nkz + k' ----
+                uint8_t *bda = sB + sb * (4 * GG::DA_B_PLANE);
+                for (int item = tid; item < 2 * kCh; item += kTcBuilders) {
+                    const int n = item % kCh, pr = item / kCh, r = n / 12, tt = n % 12;
+                    float xv[16];
+#pragma unroll
+                    for (int kk = 0; kk < 16; ++kk) {
+                        xv[kk] = 0.f;
+                        if (kk < 3 * NK) {
+                            const int i = kk / NK, kp = kk % NK;
+                            xv[kk] = sX[((i * 12 + r) * 2 + pr) * GG::XP_XS + kp * 12 + tt];
+                        }
+                    }
+                    uint32_t hv[8], lv[8];
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) {
+                        const uint2 hl = split2_bf16(xv[2 * x], xv[2 * x + 1]);
+                        hv[x] = hl.x;
+                        lv[x] = hl.y;
+                    }
+                    const uint32_t row_off = (n >> 3) * GG::DA_SBO_B + (n & 7) * 16;
+                    uint8_t *ph = bda + (2 * pr) * GG::DA_B_PLANE, *pl = ph + GG::DA_B_PLANE;
+#pragma unroll
+                    for (int gq = 0; gq < 2; ++gq) {
+                        *(uint4 *)(ph + row_off + gq * 128) = make_uint4(hv[4 * gq], hv[4 * gq + 1], hv[4 * gq + 2], hv[4 * gq + 3]);
+                        *(uint4 *)(pl + row_off + gq * 128) = make_uint4(lv[4 * gq], lv[4 * gq + 1], lv[4 * gq + 2], lv[4 * gq + 3]);
+                    }
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&bar_bready[sb]);
+
+                if (job_last) {
+                    // ---- epilogue of the job: V = acc_re + i acc_im, Sigma += sum_j V_j dH_j^+ ----
+                    if (!mbar_wait_bounded(bar_job, job_ctr & 1, kWaitNs)) {
+                        s_abort[sb] = 1;
+                        atomicExch(prm.status, 1);
+                    }
+                    ++job_ctr;
+                    tc_fence_after();
+                    builders_sync();  // every builder is done with X and B before sV overlays them
+                    const bool first_slot = vs == 0;
+                    const int pt = tid / 6, rb = (tid % 6) / EP_NSB, sbk = (tid % 6) % EP_NSB;
+                    const int e = pt / NK, k = pt % NK, E = E0 + e;
+                    const bool live = tid < NK * GG::TE * 6 && E < d.ne;
+                    for (int h = 0; h < EP_PARTS; ++h) {
+                        // the slots summed so far, fetched before the drain so their latency overlaps it
+                        CT *dst[2];
+                        CT old[2][EP_S];
+#pragma unroll
+                        for (int rl = 0; rl < 2; ++rl) {
+                            const int r = EP_R * h + 2 * rb + rl;
+                            dst[rl] = S + (((size_t)k * d.ne + (live ? E : 0)) * d.na + a) * kCh + r * 12 + EP_S * sbk;
+#pragma unroll
+                            for (int s2 = 0; s2 < EP_S; ++s2) {
+                                old[rl][s2].x = 0;
+                                old[rl][s2].y = 0;
+                                if (live && !first_slot) old[rl][s2] = dst[rl][s2];
+                            }
+                        }
+                        {
+                            const int qd = warp & 3, q = warp >> 2;
+                            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (q ? kAccIm : 0u) + EP_COLS * h;
+                            float *vrow = sV + (q * kRowsMax + qd * 32 + lane) * EP_STRIDE;
+#pragma unroll
+                            for (int c0 = 0; c0 < EP_COLS; c0 += 8) {
+                                float v[8];
+                                tmem_ld8(taddr + c0, v);
+                                tmem_ld_wait();
+#pragma unroll
+                                for (int x = 0; x < 8; ++x) vrow[c0 + x] = v[x];
+                            }
+                        }
+                        builders_sync();
+                        if (tid < NK * GG::TE * 6) {
+                            float2 acc[2][EP_S];
+#pragma unroll
+                            for (int rl = 0; rl < 2; ++rl)
+#pragma unroll
+                                for (int s2 = 0; s2 < EP_S; ++s2) acc[rl][s2] = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) {
+                                const int m = (k * 3 + j) * GG::DA_TE + e;
+                                const float *vre = sV + m * EP_STRIDE, *vim = sV + (kRowsMax + m) * EP_STRIDE;
+#pragma unroll
+                                for (int tt = 0; tt < 12; ++tt) {
+                                    float2 vv[2];
+#pragma unroll
+                                    for (int rl = 0; rl < 2; ++rl) {
+                                        const int col = (2 * rb + rl) * 12 + tt;
+                                        vv[rl] = make_float2(vre[col], vim[col]);
+                                    }
+#pragma unroll
+                                    for (int s2 = 0; s2 < EP_S; ++s2) {
+                                        const float2 hv = sDh[dh_at(j, EP_S * sbk + s2, tt)];
+#pragma unroll
+                                        for (int rl = 0; rl < 2; ++rl) acc[rl][s2] = cmul_conj_acc(acc[rl][s2], vv[rl], hv);
+                                    }
+                                }
+                            }
+                            if (live) {
+#pragma unroll
+                                for (int rl = 0; rl < 2; ++rl)
+#pragma unroll
+                                    for (int s2 = 0; s2 < EP_S; ++s2)
+                                        dst[rl][s2] = slot_sum<CT>(acc[rl][s2], old[rl][s2], first_slot);
+                            }
+                        }
+                        builders_sync();
+                    }
+                    tc_fence_before();
+                }
+                builders_sync();
+                if (s_abort[sb]) break;
+            }
+        }
+        g_base += total;
+        __syncthreads();
+        if (s_abort[0] || s_abort[1] || *s_abort_ctl) {
+            abort = true;
+            break;
+        }
+    }  // units
+
+    // ---- teardown: nothing of ours may still be in flight when the CTA exits ----
+    if (abort && ctl && lane == 0) {
+        mma_commit(bar_fin);  // arrives once every MMA issued so far is done
+        mbar_wait_bounded(bar_fin, 0, kWaitNs);
+        for (int b = 0; b < kTcRing; ++b)
+            if (last_g[b] >= 0) mbar_wait_bounded(&bar_g[b], (last_g[b] / kTcRing) & 1, kWaitNs);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// Shared memory of the warp-specialised kernel: B stages and the X buffer (the epilogue's
+// drained accumulators overlay both), the G-slice ring, the pre-product's dH operand, the
+// direct table, dH and the barriers.
+uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
+    using GG = Geo<5>;
+    uint32_t off = 0;
+    auto take = [&](uint32_t bytes, uint32_t align) {
+        off = (off + align - 1) / align * align;
+        const uint32_t at = off;
+        off += bytes;
+        return at;
+    };
+    const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
+    const uint32_t bx = bsz + 72 * GG::XP_XS * 4, nv = 2 * kRowsMax * (kCh / 3 + 1) * 4;
+    prm.off_b = take(bx > nv ? bx : nv, 1024);
+    prm.off_x = prm.off_b + bsz;
+    prm.off_g = take(kTcRing * GG::XP_SLICE, 1024);
+    prm.off_a = take(2 * 8192, 1024);
+    const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
+    prm.off_df = take(2u * 2u * GG::DA_GROUPS * 2u * rows * 16u, 1024);
+    prm.off_dh = take(3 * kDhJ * 8, 16);
+    prm.off_bar = take(128 + 8 + 2 * kMaxSlots * 4, 8);
+    prm.g_stage = 0;
+    if ((uint32_t)(5 * d.nw * 9 * 8) > bsz) return 0xFFFFFFFFu;
+    return off;
+}
+
 template <int NK>
 uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm, bool v3) {
     using GG = Geo<NK>;
@@ -919,12 +1476,14 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm, bool v3)
         // B stages, raw G (or the pre-product's G slices and dH operand and X buffer), the
         // direct table (the drained accumulators overlay it)
         const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
-        prm.off_b = take(bsz, 1024);
         if (v3) {
+            const uint32_t bx = bsz + 72 * GG::XP_XS * 4, nv3 = 2 * kRowsMax * (kCh / 3 + 1) * 4;
+            prm.off_b = take(bx > nv3 ? bx : nv3, 1024);
+            prm.off_x = prm.off_b + bsz;
             prm.off_g = take(3 * GG::XP_SLICE, 1024);
             prm.off_a = take(2 * 8192, 1024);
-            prm.off_x = take(72 * GG::XP_XS * 4, 16);
         } else {
+            prm.off_b = take(bsz, 1024);
             prm.off_a = prm.off_b;
             prm.off_g = take(2 * prm.g_stage, 128);
             prm.off_x = 0;
@@ -988,7 +1547,7 @@ long long inst_units(const InstDesc &I) { return (long long)I.nsign * I.na * I.n
 template <int NK, typename CT, bool V3>
 sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *status) {
     using GG = Geo<NK>;
-    smem = mixed_smem_bytes<NK>(d, sizeof(CT), prm, V3);
+    smem = V3 ? tc_smem_bytes(d, prm) : mixed_smem_bytes<NK>(d, sizeof(CT), prm, false);
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
         return SSE_E_INVALID_ARG;
@@ -998,8 +1557,12 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
     prm.nw = d.nw;
     prm.omega_first = d.omega_first;
     prm.nst = (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
-    cudaError_t e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT, V3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e;
+    if constexpr (V3)
+        e = cudaFuncSetAttribute(sse_tc_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
+        e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed kernel)");
     return SSE_OK;
 }
@@ -1050,7 +1613,10 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
         rs = split_g<CT>(p, io, st);
         if (rs != SSE_OK) return rs;
     }
-    sse_mixed_kernel<NK, CT, V3><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
+    if constexpr (V3)
+        sse_tc_kernel<CT><<<(unsigned)prm.total_units, kTcThreads, smem, st>>>(prm);
+    else
+        sse_mixed_kernel<NK, CT, false><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch sse_mixed_kernel");
     p.tile_e = GG::TE;
@@ -1090,7 +1656,10 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return cuda_fail(e, "reset the work counter");
         const long long grid = units < sms ? units : sms;
-        sse_mixed_kernel<NK, CT, V3><<<(unsigned)grid, kThreads, smem, st>>>(prm);
+        if constexpr (V3)
+            sse_tc_kernel<CT><<<(unsigned)grid, kTcThreads, smem, st>>>(prm);
+        else
+            sse_mixed_kernel<NK, CT, false><<<(unsigned)grid, kThreads, smem, st>>>(prm);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "launch persistent sse_mixed_kernel");
     }
@@ -1160,7 +1729,7 @@ sse_status mixed_plan_init(Plan &p) {
         case 2: smem = mixed_smem_bytes<2>(d, cb, prm, false); p.tile_e = tile_e_of<2>(); break;
         case 3: smem = mixed_smem_bytes<3>(d, cb, prm, false); p.tile_e = tile_e_of<3>(); break;
         case 4: smem = mixed_smem_bytes<4>(d, cb, prm, false); p.tile_e = tile_e_of<4>(); break;
-        default: smem = mixed_smem_bytes<5>(d, cb, prm, true); p.tile_e = tile_e_of<5>(); break;
+        default: smem = tc_smem_bytes(d, prm); p.tile_e = tile_e_of<5>(); break;
     }
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
