@@ -98,7 +98,7 @@ struct MixParams {
     int32_t nst;            // stages per job
     int32_t n_inst;
     long long total_units;
-    uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, off_x, g_stage;
+    uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, off_x, off_bp, g_stage;
     InstDesc inst[kMaxInst];
 };
 
@@ -937,25 +937,43 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // warp whose lane 0 issues the bulk copies of the G slices and every MMA.  Hand-offs go
 // through mbarriers: builders -> control "B of stage g ready" and "slot tables ready";
 // control -> builders through MMA commits ("X of stage g ready", "job accumulated").
-// In-order completion of one thread's MMAs gives the rest: the commit of stage g's
-// pre-product is issued after stage g-2's main MMAs, so its arrival also frees that
-// stage's B buffer, and the G-slice ring slot it used two stages later.
-constexpr int kTcBuilders = 256;
+// The pre-product of stage g + 2 is issued as soon as B of stage g is ready (the builders
+// have drained its TMEM buffer by then), ahead of stage g's main MMAs, so the builders never
+// wait for X while the tensor pipe has work.  The product with dH_j^dagger at the end of a
+// job runs on the tensor cores too: the builders re-encode the accumulators tile by tile
+// (bf16 hi / lo, three products as elsewhere) and the control warp issues its MMAs.
+constexpr int kTcBuilders = 384;
 constexpr int kTcThreads = kTcBuilders + 32;
 constexpr int kTcRing = 4;   // G slices in flight
 constexpr int kDhJ = 160;    // float2 per direction j of the padded dH copy
+constexpr int kXs = 76;      // row stride (floats) of the X buffer
+// Post-product Sigma_slot[(e, k), r, s] = sum_{j, t} V_j[(e, k)][r, t] conj(dH_j[s, t]) on the
+// tensor cores: rows (r', e, k) of an M tile (three rows r per tile, four tiles), K = (j, t,
+// re/im of V) = 72 padded to 80, N = (s, re/im of the product) = 24 padded to 32.
+constexpr int kPostK = 80, kPostKc = kPostK / 8;            // K and its 16-byte chunks
+constexpr uint32_t kPostSbo = kPostKc * 128;                // bytes between 8-row groups
+constexpr uint32_t kPostAPlane = (kRowsMax / 8) * kPostSbo;  // 20480
+constexpr uint32_t kPostBPlane = (32 / 8) * kPostSbo;        // 5120
+constexpr uint32_t kPostCol0 = 160, kPostCol1 = 416;        // post-product accumulators (32 columns)
+constexpr int kTcBarBytes = 192;  // 16 mbarriers, the TMEM address and the flags; the unit index follows
+
+// Row of the X buffer that holds pre-product row m = (i, r, re/im): rows ordered
+// (re/im, i, r), so that the B build reads (consecutive channels (r, t)) and the drain's
+// 16-byte writes (eight consecutive rows m) both hit distinct banks with a stride of 76.
+__device__ __forceinline__ int x_row(int m) {
+    const int pr = m & 1, ir = m >> 1;  // ir = i * 12 + r
+    return pr * 36 + ir;
+}
 
 // dH_j[s, t] in shared memory: rows s in blocks of 4 with 4 float2 of padding between
 // blocks, so the epilogue's three row blocks read distinct banks.
 __device__ __forceinline__ int dh_at(int j, int s, int t) { return j * kDhJ + s * 12 + t + (s >> 2) * 4; }
-__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 384;" ::: "memory"); }
 
 template <typename CT>
 __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_constant__ MixParams prm) {
     constexpr int NK = 5;
     using GG = Geo<NK>;
-    constexpr int EP_PARTS = 3, EP_COLS = kCh / EP_PARTS, EP_STRIDE = EP_COLS + 1, EP_R = EP_COLS / 12;
-    constexpr int EP_NSB = 3, EP_S = 12 / EP_NSB;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ctl = warp == kTcBuilders / 32;
@@ -965,7 +983,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 
     uint8_t *sB = smem + prm.off_b;              // [2 stages][re hi, re lo, im hi, im lo]
     float *sX = (float *)(smem + prm.off_x);     // X rows (i, r, re/im) x (k', t)
-    float *sV = (float *)(smem + prm.off_b);     // epilogue: overlays the B stages and X
+    uint8_t *sApost = smem + prm.off_b;          // epilogue: post-product A tile over the B stages and X
+    uint8_t *sBpost = smem + prm.off_bp;         // post-product B of the slot: conj(dH_j) [hi, lo]
     uint8_t *sRing = smem + prm.off_g;           // [kTcRing] re-encoded G slices
     uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
     uint8_t *sTab = smem + prm.off_df;           // direct Toeplitz table of the slot
@@ -977,14 +996,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bar_job = bars + kTcRing + 4;      // last MMAs of a job done
     uint64_t *bar_slot = bars + kTcRing + 5;     // slot tables built
     uint64_t *bar_fin = bars + kTcRing + 6;      // abort: every MMA issued so far done
-    uint32_t *s_tmem = (uint32_t *)(bars + kTcRing + 7);
+    uint64_t *bar_mma = bars + kTcRing + 7;      // [2] main MMAs of a stage done (B buffer free)
+    uint64_t *bar_apost = bars + kTcRing + 9;    // post-product A tile built
+    uint64_t *bar_post = bars + kTcRing + 10;    // [2] post-product MMAs of a tile done
+    uint32_t *s_tmem = (uint32_t *)(bars + kTcRing + 12);
+    static_assert((kTcRing + 12) * 8 + 5 * 4 <= kTcBarBytes, "barrier area");
     // abort flags: builders write slot g & 1 during stage g and all read it after the stage's
     // last barrier (the next write to that slot comes after another barrier); the control
     // warp has its own flag
     int *s_abort = (int *)(s_tmem + 1);          // [2]
     int *s_abort_ctl = s_abort + 2;
     int *s_nvalid = s_abort + 3;
-    long long *s_unit = (long long *)(smem + prm.off_bar + 128);
+    long long *s_unit = (long long *)(smem + prm.off_bar + kTcBarBytes);
     int *s_slot = (int *)(s_unit + 1);
     int *s_f = s_slot + kMaxSlots;
 
@@ -997,6 +1020,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(bar_job, 1);
         mbar_init(bar_slot, kTcBuilders);
         mbar_init(bar_fin, 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        mbar_init(bar_apost, kTcBuilders);
+        mbar_init(&bar_post[0], 1);
+        mbar_init(&bar_post[1], 1);
         fence_mbar_init();
         s_abort[0] = 0;
         s_abort[1] = 0;
@@ -1015,6 +1043,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 #pragma unroll
     for (int b = 0; b < kTcRing; ++b) last_g[b] = -1;
     int g_base = 0, job_ctr = 0, slot_ctr = 0;
+    int tile_ctr = 0;  // post-product tiles so far (phases of bar_apost / bar_post)
     bool abort = false;
     for (long long iter = 0;; ++iter) {
         __syncthreads();
@@ -1085,38 +1114,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         if (ctl) {
             // ================= control warp: bulk copies and MMAs (lane 0) =================
             if (lane == 0) {
+                const uint8_t *gws = I.gws[sign];
                 auto issue_pre = [&](int g, const Pos &q) {
-                    const int f = s_f[q.vs];
                     const int Ep = q.t * GG::TE - omega_max + q.st;
                     const long long slice =
-                        (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + f : (long long)d.ne * d.na;
-                    const int gg = g_base + g;
-                    uint64_t *bar = &bar_g[gg % kTcRing];
-                    mbar_arrive_expect_tx(bar, GG::XP_SLICE);
-                    bulk_g2s(sRing + (gg % kTcRing) * GG::XP_SLICE, I.gws[sign] + slice * GG::XP_SLICE,
-                             GG::XP_SLICE, bar);
-                    last_g[gg % kTcRing] = gg;
+                        (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + s_f[q.vs] : (long long)d.ne * d.na;
+                    const int gg = g_base + g, slot = gg % kTcRing;
+                    mbar_arrive_expect_tx(&bar_g[slot], GG::XP_SLICE);
+                    bulk_g2s(sRing + slot * GG::XP_SLICE, gws + slice * GG::XP_SLICE, GG::XP_SLICE, &bar_g[slot]);
+                    last_g[slot] = gg;
                 };
+                // descriptors: fixed parts built once; a shift of the start address is an add
+                // on the descriptor's low field (shared addresses stay below 2^18)
+                const uint64_t pa_h0 = smem_desc(smem_u32(sApre), 128, 512), pa_l0 = smem_desc(smem_u32(sApre) + 8192, 128, 512);
+                const uint64_t pb_h0 = smem_desc(smem_u32(sRing), 128, 512), pb_l0 = smem_desc(smem_u32(sRing) + 4096, 128, 512);
                 auto premma = [&](int g) -> bool {
-                    const int gg = g_base + g;
-                    if (!mbar_wait_bounded(&bar_g[gg % kTcRing], (gg / kTcRing) & 1, kWaitNs)) return false;
+                    const int gg = g_base + g, slot = gg % kTcRing;
+                    if (!mbar_wait_bounded(&bar_g[slot], (gg / kTcRing) & 1, kWaitNs)) return false;
                     tc_fence_after();
                     constexpr uint32_t idesc_x = idesc_bf16_f32(kRowsMax, GG::XP_N);
-                    const uint32_t a0 = smem_u32(sApre), b0 = smem_u32(sRing + (gg % kTcRing) * GG::XP_SLICE);
+                    const uint64_t boff = (uint64_t)((slot * GG::XP_SLICE) >> 4);
                     const uint32_t dx = tmem + ((gg & 1) ? kPreCol1 : kPreCol0);
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
-                        const uint64_t ah = smem_desc(a0 + ks * 256, 128, 512), al = smem_desc(a0 + 8192 + ks * 256, 128, 512);
-                        const uint64_t bh = smem_desc(b0 + ks * 256, 128, 512), bl = smem_desc(b0 + 4096 + ks * 256, 128, 512);
-                        mma_ss(dx, ah, bh, idesc_x, ks ? 1u : 0u);
-                        mma_ss(dx, ah, bl, idesc_x, 1u);
-                        mma_ss(dx, al, bh, idesc_x, 1u);
+                        const uint64_t ko = (uint64_t)(ks * 256 >> 4);
+                        mma_ss(dx, pa_h0 + ko, pb_h0 + boff + ko, idesc_x, ks ? 1u : 0u);
+                        mma_ss(dx, pa_h0 + ko, pb_l0 + boff + ko, idesc_x, 1u);
+                        mma_ss(dx, pa_l0 + ko, pb_h0 + boff + ko, idesc_x, 1u);
                     }
                     mma_commit(&bar_pre[gg & 1]);
                     return true;
                 };
                 Pos m{t_begin, 0, 0}, pf{t_begin, 0, 0};
-                for (int x = 0; x < kTcRing - 1 && x < total; ++x) {
+                for (int x = 0; x < kTcRing && x < total; ++x) {
                     issue_pre(x, pf);
                     advance(pf);
                 }
@@ -1124,39 +1154,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 constexpr uint32_t idesc_negb = idesc | (1u << 14);
                 const uint32_t lbo_a = (uint32_t)da_rows * 16, sbo_a = 2u * lbo_a;
                 const uint32_t tstride = (uint32_t)GG::DA_GROUPS * 2 * da_rows * 16;
+                // A (direct table) at row 0 for (re/im, hi/lo); stage st starts at row nw - 1 - st + TE - 1
+                uint64_t ta[4], tb[2][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    ta[x] = smem_desc(smem_u32(sTab) + (uint32_t)x * tstride, lbo_a, sbo_a);
+                    tb[0][x] = smem_desc(smem_u32(sB) + (uint32_t)x * GG::DA_B_PLANE, 128, GG::DA_SBO_B);
+                    tb[1][x] = smem_desc(smem_u32(sB) + (uint32_t)(4 * GG::DA_B_PLANE + x * GG::DA_B_PLANE), 128, GG::DA_SBO_B);
+                }
+                const uint64_t pp_ah = smem_desc(smem_u32(sApost), 128, kPostSbo);
+                const uint64_t pp_al = smem_desc(smem_u32(sApost) + kPostAPlane, 128, kPostSbo);
+                const uint64_t pp_bh = smem_desc(smem_u32(sBpost), 128, kPostSbo);
+                const uint64_t pp_bl = smem_desc(smem_u32(sBpost) + kPostBPlane, 128, kPostSbo);
+                const int ntl = t_end - t_begin;
                 bool ok = true;
                 for (int g = 0; g < total; ++g, advance(m)) {
                     const int gg = g_base + g;
                     const bool job_first = m.st == 0, job_last = m.st == prm.nst - 1;
                     const bool slot_first = job_first && m.t == t_begin;
-                    const bool slot_last = job_last && m.t + 1 == t_end;
+                    // stages after this one that still belong to its slot
+                    const int slot_rem = (t_begin + ntl - 1 - m.t) * prm.nst + (prm.nst - 1 - m.st);
                     if (slot_first) {
                         ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs);
                         ++slot_ctr;
                         if (!ok) break;
                         tc_fence_after();
                         if (!(ok = premma(g))) break;
+                        if (slot_rem >= 1 && !(ok = premma(g + 1))) break;
                     }
                     if (!(ok = mbar_wait_bounded(&bar_bready[gg & 1], (gg >> 1) & 1, kWaitNs))) break;
                     tc_fence_after();
-                    if (g + kTcRing - 1 < total) {
-                        issue_pre(g + kTcRing - 1, pf);
-                        advance(pf);
-                    }
-                    // the next stage's pre-product first, so its X is ready while these MMAs run
-                    if (!slot_last && g + 1 < total && !(ok = premma(g + 1))) break;
-                    // A: windows of the direct table starting at row (nw - 1 - st) + (TE - 1)
-                    const uint32_t r_start = (uint32_t)(nw - 1 - m.st + GG::DA_TE - 1);
-                    const uint32_t tab0 = smem_u32(sTab) + r_start * 16;
-                    auto adesc = [&](int q, int split) {
-                        return smem_desc(tab0 + (uint32_t)(q * 2 + split) * tstride, lbo_a, sbo_a);
-                    };
-                    const uint32_t b0 = smem_u32(sB + (gg & 1) * (4 * GG::DA_B_PLANE));
-                    auto bdesc = [&](int q, int split) {
-                        return smem_desc(b0 + (uint32_t)(q * 2 + split) * GG::DA_B_PLANE, 128, GG::DA_SBO_B);
-                    };
-                    const uint64_t are_h = adesc(0, 0), are_l = adesc(0, 1), aim_h = adesc(1, 0), aim_l = adesc(1, 1);
-                    const uint64_t bre_h = bdesc(0, 0), bre_l = bdesc(0, 1), bim_h = bdesc(1, 0), bim_l = bdesc(1, 1);
+                    // X of stage g + 2 ahead of this stage's main MMAs: its TMEM buffer was drained
+                    // in stage g, and its G slice was requested two stages ago
+                    if (slot_rem >= 2 && !(ok = premma(g + 2))) break;
+                    const uint64_t r_start = (uint64_t)(nw - 1 - m.st + GG::DA_TE - 1);
+                    const uint64_t are_h = ta[0] + r_start, are_l = ta[1] + r_start;
+                    const uint64_t aim_h = ta[2] + r_start, aim_l = ta[3] + r_start;
+                    const int bb = gg & 1;
+                    const uint64_t bre_h = tb[bb][0], bre_l = tb[bb][1], bim_h = tb[bb][2], bim_l = tb[bb][3];
                     const uint32_t dre = tmem, dim = tmem + kAccIm;
                     const uint32_t acc0 = job_first ? 0u : 1u;
                     // Re V = Re T Re X - Im T Im X
@@ -1173,7 +1208,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     mma_ss(dim, are_h, bim_h, idesc, 1u);
                     mma_ss(dim, are_h, bim_l, idesc, 1u);
                     mma_ss(dim, are_l, bim_h, idesc, 1u);
-                    if (job_last) mma_commit(bar_job);
+                    mma_commit(&bar_mma[bb]);
+                    // ring slot of stage g is free: its pre-product completed before the builders
+                    // reported B of stage g ready
+                    if (g + kTcRing < total) {
+                        issue_pre(g + kTcRing, pf);
+                        advance(pf);
+                    }
+                    if (job_last) {
+                        mma_commit(bar_job);
+                        // post-product of the job, one M tile at a time as the builders fill it
+                        constexpr uint32_t idesc_p = idesc_bf16_f32(kRowsMax, 32);
+                        for (int q = 0; q < 4 && ok; ++q, ++tile_ctr) {
+                            if (!(ok = mbar_wait_bounded(bar_apost, tile_ctr & 1, kWaitNs))) break;
+                            tc_fence_after();
+                            const uint32_t dp = tmem + ((tile_ctr & 1) ? kPostCol1 : kPostCol0);
+#pragma unroll
+                            for (int ks = 0; ks < kPostK / 16; ++ks) {
+                                const uint64_t ko = (uint64_t)(ks * 256 >> 4);
+                                mma_ss(dp, pp_ah + ko, pp_bh + ko, idesc_p, ks ? 1u : 0u);
+                                mma_ss(dp, pp_ah + ko, pp_bl + ko, idesc_p, 1u);
+                                mma_ss(dp, pp_al + ko, pp_bh + ko, idesc_p, 1u);
+                            }
+                            mma_commit(&bar_post[tile_ctr & 1]);
+                        }
+                        if (!ok) break;
+                    }
                 }
                 if (!ok) {
                     *s_abort_ctl = 1;
@@ -1269,6 +1329,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         *(uint4 *)(dst + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
+                    // post-product B[(s, c'), (j, t, c)]: V conj(H) = (Vr Hr + Vi Hi) + i (Vi Hr - Vr Hi)
+                    for (int x = tid; x < 32 * kPostKc; x += kTcBuilders) {
+                        const int row = x / kPostKc, kc = x % kPostKc, s2 = row >> 1, cp = row & 1;
+                        float v[8];
+#pragma unroll
+                        for (int xx = 0; xx < 8; ++xx) {
+                            const int kk = kc * 8 + xx;
+                            float val = 0.f;
+                            if (row < 24 && kk < 72) {
+                                const int j = kk / 24, t = (kk % 24) >> 1, c = kk & 1;
+                                const float2 h = sDh[dh_at(j, s2, t)];
+                                val = cp ? (c ? h.x : -h.y) : (c ? h.y : h.x);
+                            }
+                            v[xx] = val;
+                        }
+                        uint32_t hv[4], lv[4];
+#pragma unroll
+                        for (int xx = 0; xx < 4; ++xx) {
+                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+                            hv[xx] = hl.x;
+                            lv[xx] = hl.y;
+                        }
+                        uint8_t *dst = sBpost + (row >> 3) * kPostSbo + kc * 128 + (row & 7) * 16;
+                        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *(uint4 *)(dst + kPostBPlane) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    }
                     fence_proxy_async_smem();
                     mbar_arrive(bar_slot);
                 }
@@ -1280,23 +1366,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 }
                 tc_fence_after();
                 if ((warp & 3) < 3) {
-                    const int half = warp >> 2;  // columns 0..31 or 32..59
+                    const int cb = warp >> 2;  // 20-column block of the 60 columns (k', t)
                     const uint32_t taddr =
-                        tmem + ((uint32_t)((warp & 3) * 32) << 16) + (sb ? kPreCol1 : kPreCol0) + 32 * half;
+                        tmem + ((uint32_t)((warp & 3) * 32) << 16) + (sb ? kPreCol1 : kPreCol0) + 20 * cb;
                     const int m = (warp & 3) * 32 + lane;
-                    uint32_t xr[32];
-                    tmem_ld32(taddr, xr);
+                    uint32_t xr[20];
+                    tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(xr));
+                    tmem_ld4(taddr + 16, *reinterpret_cast<uint32_t(*)[4]>(xr + 16));
                     tmem_ld_wait();
                     if (m < 72) {
-                        float *row = sX + m * GG::XP_XS + 32 * half;
-                        const int ncol = half ? NK * 12 - 32 : 32;
+                        float4 *row = (float4 *)(sX + x_row(m) * kXs + 20 * cb);
 #pragma unroll
-                        for (int x = 0; x < 32; ++x)
-                            if (x < ncol) row[x] = __uint_as_float(xr[x]);
+                        for (int x = 0; x < 5; ++x)
+                            row[x] = make_float4(__uint_as_float(xr[4 * x]), __uint_as_float(xr[4 * x + 1]),
+                                                 __uint_as_float(xr[4 * x + 2]), __uint_as_float(xr[4 * x + 3]));
                     }
                     tc_fence_before();
                 }
                 builders_sync();
+                // ---- the B buffer must be free: main MMAs of stage g - 2 complete ----
+                if (gg >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((gg >> 1) - 1) & 1, kWaitNs)) {
+                    s_abort[sb] = 1;
+                    atomicExch(prm.status, 1);
+                }
                 // ---- X -> B planes [re, im][hi, lo] of channel n = (r, t), K index i * Nkz + k' ----
                 uint8_t *bda = sB + sb * (4 * GG::DA_B_PLANE);
                 for (int item = tid; item < 2 * kCh; item += kTcBuilders) {
@@ -1307,7 +1399,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         xv[kk] = 0.f;
                         if (kk < 3 * NK) {
                             const int i = kk / NK, kp = kk % NK;
-                            xv[kk] = sX[((i * 12 + r) * 2 + pr) * GG::XP_XS + kp * 12 + tt];
+                            xv[kk] = sX[x_row((i * 12 + r) * 2 + pr) * kXs + kp * 12 + tt];
                         }
                     }
                     uint32_t hv[8], lv[8];
@@ -1329,84 +1421,108 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 mbar_arrive(&bar_bready[sb]);
 
                 if (job_last) {
-                    // ---- epilogue of the job: V = acc_re + i acc_im, Sigma += sum_j V_j dH_j^+ ----
+                    // ---- epilogue of the job: Sigma += sum_j V_j dH_j^dagger (V = acc_re + i acc_im) ----
                     if (!mbar_wait_bounded(bar_job, job_ctr & 1, kWaitNs)) {
                         s_abort[sb] = 1;
                         atomicExch(prm.status, 1);
                     }
                     ++job_ctr;
                     tc_fence_after();
-                    builders_sync();  // every builder is done with X and B before sV overlays them
+                    builders_sync();  // every builder is done with X and B before the A tile overlays them
                     const bool first_slot = vs == 0;
-                    const int pt = tid / 6, rb = (tid % 6) / EP_NSB, sbk = (tid % 6) % EP_NSB;
-                    const int e = pt / NK, k = pt % NK, E = E0 + e;
-                    const bool live = tid < NK * GG::TE * 6 && E < d.ne;
-                    for (int h = 0; h < EP_PARTS; ++h) {
-                        // the slots summed so far, fetched before the drain so their latency overlaps it
-                        CT *dst[2];
-                        CT old[2][EP_S];
+                    // A-tile role: warp -> (lane quarter, row r' of the tile); lane -> accumulator row
+                    const int aq = warp & 3, arl = warp >> 2;  // arl == 3: no A-tile work
+                    const int am = aq * 32 + lane;
+                    const int ak = am / 24, aj = (am / 8) % 3, ae = am % 8;
+                    // drain role: warp -> (lane quarter = tile rows, 8 of the 24 columns = 4 values s)
+                    const int dq = warp & 3, dsub = warp >> 2;
+                    const int drow = dq * 32 + lane;  // tile row (r', e, k)
+                    const int drl = drow / 40, de = (drow / 5) % 8, dk = drow % 5;
+                    const bool dlive = drow < 120 && E0 + de < d.ne;
+                    CT old[4];
+                    CT *ddst = S;
 #pragma unroll
-                        for (int rl = 0; rl < 2; ++rl) {
-                            const int r = EP_R * h + 2 * rb + rl;
-                            dst[rl] = S + (((size_t)k * d.ne + (live ? E : 0)) * d.na + a) * kCh + r * 12 + EP_S * sbk;
-#pragma unroll
-                            for (int s2 = 0; s2 < EP_S; ++s2) {
-                                old[rl][s2].x = 0;
-                                old[rl][s2].y = 0;
-                                if (live && !first_slot) old[rl][s2] = dst[rl][s2];
+                    for (int s2 = 0; s2 < 4; ++s2) {
+                        old[s2].x = 0;
+                        old[s2].y = 0;
+                    }
+                    for (int q = 0; q <= 4; ++q) {
+                        const int tq = tile_ctr + q;  // CTA-wide index of tile q
+                        if (q > 0) {
+                            // MMAs of tile q - 1 done: its result can be drained, the A tile reused
+                            if (!mbar_wait_bounded(&bar_post[(tq - 1) & 1], ((tq - 1) >> 1) & 1, kWaitNs)) {
+                                s_abort[sb] = 1;
+                                atomicExch(prm.status, 1);
                             }
+                            tc_fence_after();
                         }
-                        {
-                            const int qd = warp & 3, q = warp >> 2;
-                            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (q ? kAccIm : 0u) + EP_COLS * h;
-                            float *vrow = sV + (q * kRowsMax + qd * 32 + lane) * EP_STRIDE;
+                        CT *nd = S;
+                        CT nold[4];
 #pragma unroll
-                            for (int c0 = 0; c0 < EP_COLS; c0 += 8) {
-                                float v[8];
-                                tmem_ld8(taddr + c0, v);
+                        for (int s2 = 0; s2 < 4; ++s2) {
+                            nold[s2].x = 0;
+                            nold[s2].y = 0;
+                        }
+                        if (q < 4) {
+                            // the slots summed so far for the rows this thread drains from tile q
+                            const int r = 3 * q + drl;
+                            nd = S + (((size_t)dk * d.ne + (dlive ? E0 + de : 0)) * d.na + a) * kCh + r * 12 + 4 * dsub;
+#pragma unroll
+                            for (int s2 = 0; s2 < 4; ++s2)
+                                if (dlive && !first_slot) nold[s2] = nd[s2];
+                            // ---- A tile q: rows (r', e, k), K = (j, t, re/im), bf16 hi / lo ----
+                            if (arl < 3) {
+                                const int r = 3 * q + arl;
+                                uint32_t vr[16], vi[16];
+                                tmem_ld16(tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)(r * 12), vr);
+                                tmem_ld16(tmem + ((uint32_t)(aq * 32) << 16) + kAccIm + (uint32_t)(r * 12), vi);
                                 tmem_ld_wait();
+                                if (am < 120) {
+                                    const int row = arl * 40 + ae * 5 + ak;
+                                    uint8_t *rbase = sApost + (row >> 3) * kPostSbo + (row & 7) * 16;
 #pragma unroll
-                                for (int x = 0; x < 8; ++x) vrow[c0 + x] = v[x];
-                            }
-                        }
-                        builders_sync();
-                        if (tid < NK * GG::TE * 6) {
-                            float2 acc[2][EP_S];
+                                    for (int cc = 0; cc < 3; ++cc) {
+                                        uint32_t hw[4], lw[4];
 #pragma unroll
-                            for (int rl = 0; rl < 2; ++rl)
-#pragma unroll
-                                for (int s2 = 0; s2 < EP_S; ++s2) acc[rl][s2] = make_float2(0.f, 0.f);
-#pragma unroll
-                            for (int j = 0; j < 3; ++j) {
-                                const int m = (k * 3 + j) * GG::DA_TE + e;
-                                const float *vre = sV + m * EP_STRIDE, *vim = sV + (kRowsMax + m) * EP_STRIDE;
-#pragma unroll
-                                for (int tt = 0; tt < 12; ++tt) {
-                                    float2 vv[2];
-#pragma unroll
-                                    for (int rl = 0; rl < 2; ++rl) {
-                                        const int col = (2 * rb + rl) * 12 + tt;
-                                        vv[rl] = make_float2(vre[col], vim[col]);
+                                        for (int x = 0; x < 4; ++x) {
+                                            const int t = 4 * cc + x;
+                                            const uint2 hl = split2_bf16(__uint_as_float(vr[t]), __uint_as_float(vi[t]));
+                                            hw[x] = hl.x;
+                                            lw[x] = hl.y;
+                                        }
+                                        uint8_t *dst = rbase + (aj * 3 + cc) * 128;
+                                        *(uint4 *)dst = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                                        *(uint4 *)(dst + kPostAPlane) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                                     }
-#pragma unroll
-                                    for (int s2 = 0; s2 < EP_S; ++s2) {
-                                        const float2 hv = sDh[dh_at(j, EP_S * sbk + s2, tt)];
-#pragma unroll
-                                        for (int rl = 0; rl < 2; ++rl) acc[rl][s2] = cmul_conj_acc(acc[rl][s2], vv[rl], hv);
+                                    if (aj == 2) {  // K 72..79: zero
+                                        *(uint4 *)(rbase + 9 * 128) = make_uint4(0u, 0u, 0u, 0u);
+                                        *(uint4 *)(rbase + 9 * 128 + kPostAPlane) = make_uint4(0u, 0u, 0u, 0u);
                                     }
                                 }
                             }
-                            if (live) {
+                        }
+                        // ---- result of tile q - 1: rows (r', e, k) x (s, re/im) -> Sigma ----
+                        if (q > 0) {
+                            float pv[8];
+                            tmem_ld8(tmem + ((uint32_t)(dq * 32) << 16) + (((tq - 1) & 1) ? kPostCol1 : kPostCol0) +
+                                         (uint32_t)(8 * dsub), pv);
+                            tmem_ld_wait();
+                            if (dlive) {
 #pragma unroll
-                                for (int rl = 0; rl < 2; ++rl)
-#pragma unroll
-                                    for (int s2 = 0; s2 < EP_S; ++s2)
-                                        dst[rl][s2] = slot_sum<CT>(acc[rl][s2], old[rl][s2], first_slot);
+                                for (int s2 = 0; s2 < 4; ++s2)
+                                    ddst[s2] = slot_sum<CT>(make_float2(pv[2 * s2], pv[2 * s2 + 1]), old[s2], first_slot);
                             }
                         }
-                        builders_sync();
+                        tc_fence_before();
+                        if (q < 4) {
+                            fence_proxy_async_smem();
+                            mbar_arrive(bar_apost);
+                        }
+                        ddst = nd;
+#pragma unroll
+                        for (int s2 = 0; s2 < 4; ++s2) old[s2] = nold[s2];
                     }
-                    tc_fence_before();
+                    tile_ctr += 4;
                 }
                 builders_sync();
                 if (s_abort[sb]) break;
@@ -1445,7 +1561,7 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
         return at;
     };
     const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
-    const uint32_t bx = bsz + 72 * GG::XP_XS * 4, nv = 2 * kRowsMax * (kCh / 3 + 1) * 4;
+    const uint32_t bx = bsz + 72 * kXs * 4, nv = 2 * kPostAPlane;
     prm.off_b = take(bx > nv ? bx : nv, 1024);
     prm.off_x = prm.off_b + bsz;
     prm.off_g = take(kTcRing * GG::XP_SLICE, 1024);
@@ -1453,7 +1569,8 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
     const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
     prm.off_df = take(2u * 2u * GG::DA_GROUPS * 2u * rows * 16u, 1024);
     prm.off_dh = take(3 * kDhJ * 8, 16);
-    prm.off_bar = take(128 + 8 + 2 * kMaxSlots * 4, 8);
+    prm.off_bp = take(2 * kPostBPlane, 1024);
+    prm.off_bar = take(kTcBarBytes + 8 + 2 * kMaxSlots * 4, 8);
     prm.g_stage = 0;
     if ((uint32_t)(5 * d.nw * 9 * 8) > bsz) return 0xFFFFFFFFu;
     return off;
@@ -1729,13 +1846,15 @@ sse_status mixed_plan_init(Plan &p) {
         case 2: smem = mixed_smem_bytes<2>(d, cb, prm, false); p.tile_e = tile_e_of<2>(); break;
         case 3: smem = mixed_smem_bytes<3>(d, cb, prm, false); p.tile_e = tile_e_of<3>(); break;
         case 4: smem = mixed_smem_bytes<4>(d, cb, prm, false); p.tile_e = tile_e_of<4>(); break;
-        default: smem = tc_smem_bytes(d, prm); p.tile_e = tile_e_of<5>(); break;
+        default: smem = mixed_smem_bytes<5>(d, cb, prm, false); p.tile_e = tile_e_of<5>(); break;
     }
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
         return SSE_E_INVALID_ARG;
     }
-    if (d.nkz == 5) {
+    // Nkz = 5: the warp-specialised tensor-core form when its tiles fit (Nw <= 40), with a
+    // workspace; otherwise the direct form above
+    if (d.nkz == 5 && tc_smem_bytes(d, prm) <= 232448u) {
         // workspace of the tensor-core pre-product: G re-encoded per sign, plus a zero slice
         const size_t sign_bytes = ((size_t)d.ne * d.na + 1) * 8192;
         cudaError_t e = cudaMalloc(&p.mixed_ws, 2 * sign_bytes);
