@@ -936,14 +936,16 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // prepared: eight builder warps (slot tables, X drain, B operand, epilogue) and one control
 // warp whose lane 0 issues the bulk copies of the G slices and every MMA.  Hand-offs go
 // through mbarriers: builders -> control "B of stage g ready" and "slot tables ready";
-// control -> builders through MMA commits ("X of stage g ready", "job accumulated").
+// control -> builders through MMA commits ("X of stage g ready", "job accumulated").  A
+// third role, one more warp, streams the G slices into a ring of four; the control warp
+// hands a ring slot back with an MMA commit once the pre-product that read it is done.
 // The pre-product of stage g + 2 is issued as soon as B of stage g is ready (the builders
 // have drained its TMEM buffer by then), ahead of stage g's main MMAs, so the builders never
 // wait for X while the tensor pipe has work.  The product with dH_j^dagger at the end of a
 // job runs on the tensor cores too: the builders re-encode the accumulators tile by tile
 // (bf16 hi / lo, three products as elsewhere) and the control warp issues its MMAs.
 constexpr int kTcBuilders = 384;
-constexpr int kTcThreads = kTcBuilders + 32;
+constexpr int kTcThreads = kTcBuilders + 64;  // + control warp + bulk-copy warp
 constexpr int kTcRing = 4;   // G slices in flight
 constexpr int kDhJ = 160;    // float2 per direction j of the padded dH copy
 constexpr int kXs = 76;      // row stride (floats) of the X buffer
@@ -955,7 +957,7 @@ constexpr uint32_t kPostSbo = kPostKc * 128;                // bytes between 8-r
 constexpr uint32_t kPostAPlane = (kRowsMax / 8) * kPostSbo;  // 20480
 constexpr uint32_t kPostBPlane = (32 / 8) * kPostSbo;        // 5120
 constexpr uint32_t kPostCol0 = 160, kPostCol1 = 416;        // post-product accumulators (32 columns)
-constexpr int kTcBarBytes = 192;  // 16 mbarriers, the TMEM address and the flags; the unit index follows
+constexpr int kTcBarBytes = 192;  // 20 mbarriers, the TMEM address and the flags; the unit index follows
 
 // Row of the X buffer that holds pre-product row m = (i, r, re/im): rows ordered
 // (re/im, i, r), so that the B build reads (consecutive channels (r, t)) and the drain's
@@ -976,7 +978,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     using GG = Geo<NK>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool ctl = warp == kTcBuilders / 32;
+    const bool ctl = warp == kTcBuilders / 32;      // control warp
+    const bool prd = warp == kTcBuilders / 32 + 1;  // bulk-copy warp
     const int nw = prm.nw;
     const int omega_max = prm.omega_first + nw - 1;
     const int da_rows = nw + 2 * GG::DA_TE - 2;
@@ -999,14 +1002,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bar_mma = bars + kTcRing + 7;      // [2] main MMAs of a stage done (B buffer free)
     uint64_t *bar_apost = bars + kTcRing + 9;    // post-product A tile built
     uint64_t *bar_post = bars + kTcRing + 10;    // [2] post-product MMAs of a tile done
-    uint32_t *s_tmem = (uint32_t *)(bars + kTcRing + 12);
-    static_assert((kTcRing + 12) * 8 + 5 * 4 <= kTcBarBytes, "barrier area");
+    uint64_t *bar_empty = bars + kTcRing + 12;   // [kTcRing] pre-product done with a ring slot
+    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 12);
+    static_assert((2 * kTcRing + 12) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
     // abort flags: builders write slot g & 1 during stage g and all read it after the stage's
     // last barrier (the next write to that slot comes after another barrier); the control
     // warp has its own flag
     int *s_abort = (int *)(s_tmem + 1);          // [2]
     int *s_abort_ctl = s_abort + 2;
     int *s_nvalid = s_abort + 3;
+    int *s_abort_prd = s_abort + 4;
     long long *s_unit = (long long *)(smem + prm.off_bar + kTcBarBytes);
     int *s_slot = (int *)(s_unit + 1);
     int *s_f = s_slot + kMaxSlots;
@@ -1025,10 +1030,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(bar_apost, kTcBuilders);
         mbar_init(&bar_post[0], 1);
         mbar_init(&bar_post[1], 1);
+        for (int b = 0; b < kTcRing; ++b) mbar_init(&bar_empty[b], 1);
         fence_mbar_init();
         s_abort[0] = 0;
         s_abort[1] = 0;
         *s_abort_ctl = 0;
+        *s_abort_prd = 0;
     }
     if (warp == 0) {
         tmem_alloc(s_tmem, kTmemCols);
@@ -1039,7 +1046,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    int last_g[kTcRing];  // control lane 0: last stage copied into each ring slot
+    int last_g[kTcRing];  // bulk-copy lane 0: last stage copied into each ring slot
 #pragma unroll
     for (int b = 0; b < kTcRing; ++b) last_g[b] = -1;
     int g_base = 0, job_ctr = 0, slot_ctr = 0;
@@ -1114,16 +1121,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         if (ctl) {
             // ================= control warp: bulk copies and MMAs (lane 0) =================
             if (lane == 0) {
-                const uint8_t *gws = I.gws[sign];
-                auto issue_pre = [&](int g, const Pos &q) {
-                    const int Ep = q.t * GG::TE - omega_max + q.st;
-                    const long long slice =
-                        (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + s_f[q.vs] : (long long)d.ne * d.na;
-                    const int gg = g_base + g, slot = gg % kTcRing;
-                    mbar_arrive_expect_tx(&bar_g[slot], GG::XP_SLICE);
-                    bulk_g2s(sRing + slot * GG::XP_SLICE, gws + slice * GG::XP_SLICE, GG::XP_SLICE, &bar_g[slot]);
-                    last_g[slot] = gg;
-                };
                 // descriptors: fixed parts built once; a shift of the start address is an add
                 // on the descriptor's low field (shared addresses stay below 2^18)
                 const uint64_t pa_h0 = smem_desc(smem_u32(sApre), 128, 512), pa_l0 = smem_desc(smem_u32(sApre) + 8192, 128, 512);
@@ -1143,13 +1140,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         mma_ss(dx, pa_l0 + ko, pb_h0 + boff + ko, idesc_x, 1u);
                     }
                     mma_commit(&bar_pre[gg & 1]);
+                    mma_commit(&bar_empty[slot]);  // the ring slot can be refilled
                     return true;
                 };
-                Pos m{t_begin, 0, 0}, pf{t_begin, 0, 0};
-                for (int x = 0; x < kTcRing && x < total; ++x) {
-                    issue_pre(x, pf);
-                    advance(pf);
-                }
+                Pos m{t_begin, 0, 0};
                 constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
                 constexpr uint32_t idesc_negb = idesc | (1u << 14);
                 const uint32_t lbo_a = (uint32_t)da_rows * 16, sbo_a = 2u * lbo_a;
@@ -1209,12 +1203,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     mma_ss(dim, are_h, bim_l, idesc, 1u);
                     mma_ss(dim, are_l, bim_h, idesc, 1u);
                     mma_commit(&bar_mma[bb]);
-                    // ring slot of stage g is free: its pre-product completed before the builders
-                    // reported B of stage g ready
-                    if (g + kTcRing < total) {
-                        issue_pre(g + kTcRing, pf);
-                        advance(pf);
-                    }
                     if (job_last) {
                         mma_commit(bar_job);
                         // post-product of the job, one M tile at a time as the builders fill it
@@ -1241,6 +1229,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 }
             }
             __syncwarp();
+        } else if (prd) {
+            // ================= bulk-copy warp: G slices into the ring (lane 0) =================
+            if (lane == 0) {
+                const uint8_t *gws = I.gws[sign];
+                Pos pf{t_begin, 0, 0};
+                bool ok = true;
+                for (int g = 0; g < total; ++g, advance(pf)) {
+                    const int gg = g_base + g, slot = gg % kTcRing, use = gg / kTcRing;
+                    // slot free: the pre-product of its previous stage is done (first use: free)
+                    if (!(ok = mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
+                    // the zero slice stands in for energies below or above the grid
+                    const int Ep = pf.t * GG::TE - omega_max + pf.st;
+                    const long long slice =
+                        (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + s_f[pf.vs] : (long long)d.ne * d.na;
+                    mbar_arrive_expect_tx(&bar_g[slot], GG::XP_SLICE);
+                    bulk_g2s(sRing + slot * GG::XP_SLICE, gws + slice * GG::XP_SLICE, GG::XP_SLICE, &bar_g[slot]);
+                    last_g[slot] = gg;
+                }
+                if (!ok) {
+                    *s_abort_prd = 1;
+                    atomicExch(prm.status, 1);
+                }
+            }
+            __syncwarp();
         } else {
             // ================= builder warps =================
             Pos cur{t_begin, 0, 0};
@@ -1252,6 +1264,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 const bool slot_first = job_first && t == t_begin;
                 // another CTA timed out: stop early instead of waiting out every bound
                 if (job_first && tid == 0 && *(volatile int32_t *)prm.status != 0) s_abort[sb] = 1;
+                if (job_first && vs > 0) {
+                    // the job's epilogue adds to Sigma: bring those lines to L2 while the job runs
+                    constexpr int kLines = (kCh * (int)sizeof(CT) + 127) / 128;
+                    for (int x = tid; x < NK * GG::TE * kLines; x += kTcBuilders) {
+                        const int pt = x / kLines, ln = x % kLines, k = pt / GG::TE, E = E0 + pt % GG::TE;
+                        if (E < d.ne)
+                            prefetch_l2((const uint8_t *)(S + (((size_t)k * d.ne + E) * d.na + a) * kCh) + ln * 128);
+                    }
+                }
 
                 if (slot_first) {
                     // Slot tables: dH (fp32, padded), the direct Toeplitz table of the folded,
@@ -1431,7 +1452,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     builders_sync();  // every builder is done with X and B before the A tile overlays them
                     const bool first_slot = vs == 0;
                     // A-tile role: warp -> (lane quarter, row r' of the tile); lane -> accumulator row
-                    const int aq = warp & 3, arl = warp >> 2;  // arl == 3: no A-tile work
+                    const int aq = warp & 3, arl = warp >> 2;
                     const int am = aq * 32 + lane;
                     const int ak = am / 24, aj = (am / 8) % 3, ae = am % 8;
                     // drain role: warp -> (lane quarter = tile rows, 8 of the 24 columns = 4 values s)
@@ -1440,14 +1461,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const int drl = drow / 40, de = (drow / 5) % 8, dk = drow % 5;
                     const bool dlive = drow < 120 && E0 + de < d.ne;
                     CT old[4];
-                    CT *ddst = S;
-#pragma unroll
-                    for (int s2 = 0; s2 < 4; ++s2) {
-                        old[s2].x = 0;
-                        old[s2].y = 0;
-                    }
+                    CT *dst = S;
+                    // Tile q: its A is built once the MMAs of tile q - 1 are done (one A buffer);
+                    // the accumulator columns it needs are loaded before that wait, and the FP64
+                    // update of Sigma with tile q - 1 runs after tile q is handed to the MMAs.
                     for (int q = 0; q <= 4; ++q) {
                         const int tq = tile_ctr + q;  // CTA-wide index of tile q
+                        uint32_t vr[12], vi[12];
+                        if (q < 4) {
+                            const uint32_t ta = tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)((3 * q + arl) * 12);
+                            tmem_ld8(ta, *reinterpret_cast<float(*)[8]>(vr));
+                            tmem_ld4(ta + 8, *reinterpret_cast<uint32_t(*)[4]>(vr + 8));
+                            tmem_ld8(ta + kAccIm, *reinterpret_cast<float(*)[8]>(vi));
+                            tmem_ld4(ta + kAccIm + 8, *reinterpret_cast<uint32_t(*)[4]>(vi + 8));
+                        }
                         if (q > 0) {
                             // MMAs of tile q - 1 done: its result can be drained, the A tile reused
                             if (!mbar_wait_bounded(&bar_post[(tq - 1) & 1], ((tq - 1) >> 1) & 1, kWaitNs)) {
@@ -1456,71 +1483,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             }
                             tc_fence_after();
                         }
-                        CT *nd = S;
-                        CT nold[4];
-#pragma unroll
-                        for (int s2 = 0; s2 < 4; ++s2) {
-                            nold[s2].x = 0;
-                            nold[s2].y = 0;
-                        }
-                        if (q < 4) {
-                            // the slots summed so far for the rows this thread drains from tile q
-                            const int r = 3 * q + drl;
-                            nd = S + (((size_t)dk * d.ne + (dlive ? E0 + de : 0)) * d.na + a) * kCh + r * 12 + 4 * dsub;
-#pragma unroll
-                            for (int s2 = 0; s2 < 4; ++s2)
-                                if (dlive && !first_slot) nold[s2] = nd[s2];
+                        tmem_ld_wait();
+                        if (q < 4 && am < 120) {
                             // ---- A tile q: rows (r', e, k), K = (j, t, re/im), bf16 hi / lo ----
-                            if (arl < 3) {
-                                const int r = 3 * q + arl;
-                                uint32_t vr[16], vi[16];
-                                tmem_ld16(tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)(r * 12), vr);
-                                tmem_ld16(tmem + ((uint32_t)(aq * 32) << 16) + kAccIm + (uint32_t)(r * 12), vi);
-                                tmem_ld_wait();
-                                if (am < 120) {
-                                    const int row = arl * 40 + ae * 5 + ak;
-                                    uint8_t *rbase = sApost + (row >> 3) * kPostSbo + (row & 7) * 16;
+                            const int row = arl * 40 + ae * 5 + ak;
+                            uint8_t *rbase = sApost + (row >> 3) * kPostSbo + (row & 7) * 16;
 #pragma unroll
-                                    for (int cc = 0; cc < 3; ++cc) {
-                                        uint32_t hw[4], lw[4];
+                            for (int cc = 0; cc < 3; ++cc) {
+                                uint32_t hw[4], lw[4];
 #pragma unroll
-                                        for (int x = 0; x < 4; ++x) {
-                                            const int t = 4 * cc + x;
-                                            const uint2 hl = split2_bf16(__uint_as_float(vr[t]), __uint_as_float(vi[t]));
-                                            hw[x] = hl.x;
-                                            lw[x] = hl.y;
-                                        }
-                                        uint8_t *dst = rbase + (aj * 3 + cc) * 128;
-                                        *(uint4 *)dst = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                                        *(uint4 *)(dst + kPostAPlane) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                                    }
-                                    if (aj == 2) {  // K 72..79: zero
-                                        *(uint4 *)(rbase + 9 * 128) = make_uint4(0u, 0u, 0u, 0u);
-                                        *(uint4 *)(rbase + 9 * 128 + kPostAPlane) = make_uint4(0u, 0u, 0u, 0u);
-                                    }
+                                for (int x = 0; x < 4; ++x) {
+                                    const int t = 4 * cc + x;
+                                    const uint2 hl = split2_bf16(__uint_as_float(vr[t]), __uint_as_float(vi[t]));
+                                    hw[x] = hl.x;
+                                    lw[x] = hl.y;
                                 }
+                                uint8_t *p2 = rbase + (aj * 3 + cc) * 128;
+                                *(uint4 *)p2 = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                                *(uint4 *)(p2 + kPostAPlane) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                            }
+                            if (aj == 2) {  // K 72..79: zero
+                                *(uint4 *)(rbase + 9 * 128) = make_uint4(0u, 0u, 0u, 0u);
+                                *(uint4 *)(rbase + 9 * 128 + kPostAPlane) = make_uint4(0u, 0u, 0u, 0u);
                             }
                         }
-                        // ---- result of tile q - 1: rows (r', e, k) x (s, re/im) -> Sigma ----
+                        float pv[8];
                         if (q > 0) {
-                            float pv[8];
+                            // ---- result of tile q - 1: rows (r', e, k) x (s, re/im) ----
                             tmem_ld8(tmem + ((uint32_t)(dq * 32) << 16) + (((tq - 1) & 1) ? kPostCol1 : kPostCol0) +
                                          (uint32_t)(8 * dsub), pv);
                             tmem_ld_wait();
-                            if (dlive) {
-#pragma unroll
-                                for (int s2 = 0; s2 < 4; ++s2)
-                                    ddst[s2] = slot_sum<CT>(make_float2(pv[2 * s2], pv[2 * s2 + 1]), old[s2], first_slot);
-                            }
                         }
                         tc_fence_before();
                         if (q < 4) {
                             fence_proxy_async_smem();
                             mbar_arrive(bar_apost);
                         }
-                        ddst = nd;
+                        if (q > 0 && dlive) {
 #pragma unroll
-                        for (int s2 = 0; s2 < 4; ++s2) old[s2] = nold[s2];
+                            for (int s2 = 0; s2 < 4; ++s2)
+                                dst[s2] = slot_sum<CT>(make_float2(pv[2 * s2], pv[2 * s2 + 1]), old[s2], first_slot);
+                        }
+                        if (q < 4) {
+                            // the slots summed so far for the rows this thread takes from tile q
+                            dst = S + (((size_t)dk * d.ne + (dlive ? E0 + de : 0)) * d.na + a) * kCh + (3 * q + drl) * 12 +
+                                  4 * dsub;
+#pragma unroll
+                            for (int s2 = 0; s2 < 4; ++s2) {
+                                old[s2].x = 0;
+                                old[s2].y = 0;
+                                if (dlive && !first_slot) old[s2] = dst[s2];
+                            }
+                        }
                     }
                     tile_ctr += 4;
                 }
@@ -1530,7 +1544,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         }
         g_base += total;
         __syncthreads();
-        if (s_abort[0] || s_abort[1] || *s_abort_ctl) {
+        if (s_abort[0] || s_abort[1] || *s_abort_ctl || *s_abort_prd) {
             abort = true;
             break;
         }
@@ -1540,6 +1554,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (abort && ctl && lane == 0) {
         mma_commit(bar_fin);  // arrives once every MMA issued so far is done
         mbar_wait_bounded(bar_fin, 0, kWaitNs);
+    }
+    if (abort && prd && lane == 0) {
         for (int b = 0; b < kTcRing; ++b)
             if (last_g[b] >= 0) mbar_wait_bounded(&bar_g[b], (last_g[b] / kTcRing) & 1, kWaitNs);
     }

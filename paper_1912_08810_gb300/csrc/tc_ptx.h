@@ -69,6 +69,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// Hint: bring the cache line holding `p` (inside a live allocation) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // ---- bulk copies (TMA, non-tensor form) ------------------------------------------------
 
 // 1-D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global
