@@ -89,6 +89,7 @@ struct InstDesc {
     int32_t nsign;
     long long unit_begin;
     const uint8_t *gws[2];  // tensor-core form: G re-encoded per sign (see sse_split_g_kernel)
+    const uint8_t *sws[2];  // tensor-core form: slot tables per sign (see sse_slot_tables_kernel)
 };
 
 struct MixParams {
@@ -181,6 +182,17 @@ __device__ __forceinline__ float2 slot_sum<float2>(float2 v, float2 old, bool fi
     const double y = f32_to_f64(old.y) + f32_to_f64(v.y);
     return make_float2(f64_to_f32(x), f64_to_f32(y));
 }
+
+// Running sum over neighbour slots kept in FP32 in the output element itself (its first 8
+// bytes) until the last slot, which writes the element in its own type.
+template <typename CT>
+__device__ __forceinline__ float2 *partial_of(CT *p) { return reinterpret_cast<float2 *>(p); }
+template <typename CT>
+__device__ __forceinline__ CT final_of(float2 v);
+template <>
+__device__ __forceinline__ double2 final_of<double2>(float2 v) { return make_double2(f32_to_f64(v.x), f32_to_f64(v.y)); }
+template <>
+__device__ __forceinline__ float2 final_of<float2>(float2 v) { return v; }
 
 template <int NK, typename CT, bool V3>
 __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_constant__ MixParams prm) {
@@ -972,6 +984,127 @@ __device__ __forceinline__ int x_row(int m) {
 __device__ __forceinline__ int dh_at(int j, int s, int t) { return j * kDhJ + s * 12 + t + (s >> 2) * 4; }
 __device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 384;" ::: "memory"); }
 
+// Bytes of one slot's tables in the workspace: the direct Toeplitz table (rows w0 in
+// [1 - TE, Nw + TE - 2]), the pre-product's dH operand and the post-product's conj(dH)
+// operand, each in the shared-memory layout the MMAs read.
+__host__ __device__ constexpr uint32_t tc_table_bytes(int nw) { return 2u * 2u * 16u * 2u * (uint32_t)(nw + 14) * 16u; }
+__host__ __device__ constexpr uint32_t tc_entry_bytes(int nw) { return tc_table_bytes(nw) + 16384u + 2u * kPostBPlane; }
+
+// Slot tables of one sign, one CTA per (atom a, slot b) with a neighbour: Dt folded over
+// qz onto kz' = qz mod Nkz (T depends on (k - k') mod Nkz only), the direct table of the
+// folded Dt, A_pre = the complex product dH_i . G as a real one (row re: (Re dH, -Im dH); row
+// im: (Im dH, Re dH)), and B_post[(s, c'), (j, t, c)] for V conj(dH_j) = (Vr Hr + Vi Hi) +
+// i (Vi Hr - Vr Hi); every value split into bf16 hi + lo.
+template <typename CT>
+__global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restrict__ D, const CT *__restrict__ dH,
+                                                              const int32_t *__restrict__ neigh, uint8_t *__restrict__ out,
+                                                              int na, int nb, int nqz, int nw) {
+    constexpr int NK = 5;
+    using GG = Geo<NK>;
+    extern __shared__ __align__(16) uint8_t tsm[];
+    float2 *sDh = (float2 *)tsm;                      // [3][kDhJ] padded dH_j[s, t]
+    float2 *dfold = (float2 *)(tsm + 3 * kDhJ * 8);   // [kappa][w][ij]
+    const int a = blockIdx.x / nb, b = blockIdx.x % nb, tid = threadIdx.x;
+    if (__ldg(neigh + (size_t)a * nb + b) < 0) return;
+    const int da_rows = nw + 2 * GG::DA_TE - 2;
+    uint8_t *tab = out + (size_t)blockIdx.x * tc_entry_bytes(nw);
+    uint8_t *apre = tab + tc_table_bytes(nw), *bpost = apre + 16384;
+    const CT *dh = dH + ((size_t)a * nb + b) * 3 * kCh;
+    for (int x = tid; x < 3 * kCh; x += 256) sDh[dh_at(x / kCh, (x % kCh) / 12, x % 12)] = load_c32(dh + x);
+    for (int x = tid; x < NK * nw * 9; x += 256) {
+        const int ij = x % 9, w = (x / 9) % nw, kap = x / (9 * nw);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int q = kap; q < nqz; q += NK) {
+            const float2 v = load_c32(D + ((((size_t)q * nw + w) * na + a) * nb + b) * 9 + ij);
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        dfold[x] = acc;
+    }
+    __syncthreads();
+    // direct table: [q = Re, Im][hi, lo][group (k, j)][K group][row r] x 16 bytes, entry
+    // (i, k') of row r = Re or Im of Df_ij[(k - k') mod Nkz][r - (TE - 1)]
+    const int nitems = 2 * GG::DA_GROUPS * 2 * da_rows;
+    for (int x = tid; x < nitems; x += 256) {
+        const int r = x % da_rows, kg = (x / da_rows) % 2, gq = (x / (2 * da_rows)) % GG::DA_GROUPS;
+        const int q = x / (2 * da_rows * GG::DA_GROUPS);
+        const int k = gq / 3, j = gq % 3, w0 = r - (GG::DA_TE - 1);
+        float v[8];
+#pragma unroll
+        for (int xx = 0; xx < 8; ++xx) {
+            const int kk = kg * 8 + xx;
+            float val = 0.f;
+            if (gq < 3 * NK && kk < 3 * NK && w0 >= 0 && w0 < nw) {
+                const int i = kk / NK, kp = kk % NK;
+                const float2 T = dfold[(((k - kp + NK) % NK) * nw + w0) * 9 + i * 3 + j];
+                val = q ? T.y : T.x;
+            }
+            v[xx] = val;
+        }
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int xx = 0; xx < 4; ++xx) {
+            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+            hv[xx] = hl.x;
+            lv[xx] = hl.y;
+        }
+        const size_t base_hi = ((((size_t)(q * 2 + 0) * GG::DA_GROUPS + gq) * 2 + kg) * da_rows + r) * 16;
+        const size_t base_lo = ((((size_t)(q * 2 + 1) * GG::DA_GROUPS + gq) * 2 + kg) * da_rows + r) * 16;
+        *(uint4 *)(tab + base_hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *(uint4 *)(tab + base_lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+    for (int x = tid; x < kRowsMax * 4; x += 256) {
+        const int m = x >> 2, kg = x & 3;
+        float v[8];
+#pragma unroll
+        for (int xx = 0; xx < 8; ++xx) {
+            const int kk = kg * 8 + xx;
+            float val = 0.f;
+            if (m < 72 && kk < 24) {
+                const int pr = m & 1, r = (m >> 1) % 12, i = (m >> 1) / 12, pc = kk / 12, u = kk % 12;
+                const float2 h = sDh[dh_at(i, r, u)];
+                val = pr ? (pc ? h.x : h.y) : (pc ? -h.y : h.x);
+            }
+            v[xx] = val;
+        }
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int xx = 0; xx < 4; ++xx) {
+            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+            hv[xx] = hl.x;
+            lv[xx] = hl.y;
+        }
+        uint8_t *dst = apre + (m >> 3) * 512 + kg * 128 + (m & 7) * 16;
+        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *(uint4 *)(dst + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+    for (int x = tid; x < 32 * kPostKc; x += 256) {
+        const int row = x / kPostKc, kc = x % kPostKc, s2 = row >> 1, cp = row & 1;
+        float v[8];
+#pragma unroll
+        for (int xx = 0; xx < 8; ++xx) {
+            const int kk = kc * 8 + xx;
+            float val = 0.f;
+            if (row < 24 && kk < 72) {
+                const int j = kk / 24, t = (kk % 24) >> 1, c = kk & 1;
+                const float2 h = sDh[dh_at(j, s2, t)];
+                val = cp ? (c ? h.x : -h.y) : (c ? h.y : h.x);
+            }
+            v[xx] = val;
+        }
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int xx = 0; xx < 4; ++xx) {
+            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+            hv[xx] = hl.x;
+            lv[xx] = hl.y;
+        }
+        uint8_t *dst = bpost + (row >> 3) * kPostSbo + kc * 128 + (row & 7) * 16;
+        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *(uint4 *)(dst + kPostBPlane) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+}
+
 template <typename CT>
 __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_constant__ MixParams prm) {
     constexpr int NK = 5;
@@ -991,20 +1124,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint8_t *sRing = smem + prm.off_g;           // [kTcRing] re-encoded G slices
     uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
     uint8_t *sTab = smem + prm.off_df;           // direct Toeplitz table of the slot
-    float2 *sDh = (float2 *)(smem + prm.off_dh);
     uint64_t *bars = (uint64_t *)(smem + prm.off_bar);
     uint64_t *bar_g = bars;                      // [kTcRing] slice landed
     uint64_t *bar_pre = bars + kTcRing;          // [2] pre-product of a stage done
     uint64_t *bar_bready = bars + kTcRing + 2;   // [2] B of a stage built
     uint64_t *bar_job = bars + kTcRing + 4;      // last MMAs of a job done
-    uint64_t *bar_slot = bars + kTcRing + 5;     // slot tables built
+    uint64_t *bar_slot = bars + kTcRing + 5;     // slot tables copied in
     uint64_t *bar_fin = bars + kTcRing + 6;      // abort: every MMA issued so far done
     uint64_t *bar_mma = bars + kTcRing + 7;      // [2] main MMAs of a stage done (B buffer free)
     uint64_t *bar_apost = bars + kTcRing + 9;    // post-product A tile built
     uint64_t *bar_post = bars + kTcRing + 10;    // [2] post-product MMAs of a tile done
     uint64_t *bar_empty = bars + kTcRing + 12;   // [kTcRing] pre-product done with a ring slot
-    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 12);
-    static_assert((2 * kTcRing + 12) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
+    uint64_t *bar_slotfree = bars + 2 * kTcRing + 12;  // every MMA of the previous slot done
+    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 13);
+    static_assert((2 * kTcRing + 13) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
     // abort flags: builders write slot g & 1 during stage g and all read it after the stage's
     // last barrier (the next write to that slot comes after another barrier); the control
     // warp has its own flag
@@ -1023,7 +1156,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(&bar_bready[0], kTcBuilders);
         mbar_init(&bar_bready[1], kTcBuilders);
         mbar_init(bar_job, 1);
-        mbar_init(bar_slot, kTcBuilders);
+        mbar_init(bar_slot, 1);
+        mbar_init(bar_slotfree, 1);
         mbar_init(bar_fin, 1);
         mbar_init(&bar_mma[0], 1);
         mbar_init(&bar_mma[1], 1);
@@ -1047,6 +1181,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     const uint32_t tmem = *s_tmem;
 
     int last_g[kTcRing];  // bulk-copy lane 0: last stage copied into each ring slot
+    int slot_cp = 0;      // bulk-copy lane 0: slot tables copied so far
 #pragma unroll
     for (int b = 0; b < kTcRing; ++b) last_g[b] = -1;
     int g_base = 0, job_ctr = 0, slot_ctr = 0;
@@ -1072,9 +1207,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         const long long rem = local - (long long)sign * I.na * I.nchunks;
         const int a = (int)(rem / I.nchunks), chunk = (int)(rem % I.nchunks);
         const Dims d{prm.nkz, I.nqz, I.ne, nw, I.na, I.nb, prm.omega_first};
-        const CT *__restrict__ D = (const CT *)I.D[sign];
         CT *__restrict__ S = (CT *)I.S[sign];
-        const CT *__restrict__ dH = (const CT *)I.dH;
         const int t_begin = chunk * I.tiles_per_cta;
         const int t_end = min(I.ntiles, t_begin + I.tiles_per_cta);
         if (tid == 0) {
@@ -1221,6 +1354,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             mma_commit(&bar_post[tile_ctr & 1]);
                         }
                         if (!ok) break;
+                        if (slot_rem == 0) mma_commit(bar_slotfree);  // the slot's tables can be replaced
                     }
                 }
                 if (!ok) {
@@ -1233,10 +1367,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             // ================= bulk-copy warp: G slices into the ring (lane 0) =================
             if (lane == 0) {
                 const uint8_t *gws = I.gws[sign];
+                const uint32_t tbytes = tc_table_bytes(nw), ebytes = tc_entry_bytes(nw);
                 Pos pf{t_begin, 0, 0};
                 bool ok = true;
                 for (int g = 0; g < total; ++g, advance(pf)) {
                     const int gg = g_base + g, slot = gg % kTcRing, use = gg / kTcRing;
+                    if (pf.st == 0 && pf.t == t_begin) {
+                        // a new slot: its tables replace the previous slot's once every MMA that
+                        // read those is done (the CTA's first slot: nothing to wait for)
+                        if (!(ok = mbar_wait_bounded(bar_slotfree, (slot_cp & 1) ^ 1, kWaitNs))) break;
+                        const uint8_t *src = I.sws[sign] + ((size_t)a * d.nb + s_slot[pf.vs]) * ebytes;
+                        mbar_arrive_expect_tx(bar_slot, ebytes);
+                        bulk_g2s(sTab, src, tbytes, bar_slot);
+                        bulk_g2s(sApre, src + tbytes, 16384, bar_slot);
+                        bulk_g2s(sBpost, src + tbytes + 16384, 2 * kPostBPlane, bar_slot);
+                        ++slot_cp;
+                    }
                     // slot free: the pre-product of its previous stage is done (first use: free)
                     if (!(ok = mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
                     // the zero slice stands in for energies below or above the grid
@@ -1261,9 +1407,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 const int gg = g_base + g, sb = gg & 1;
                 const int E0 = t * GG::TE;
                 const bool job_first = st == 0, job_last = st == prm.nst - 1;
-                const bool slot_first = job_first && t == t_begin;
-                // another CTA timed out: stop early instead of waiting out every bound
-                if (job_first && tid == 0 && *(volatile int32_t *)prm.status != 0) s_abort[sb] = 1;
                 if (job_first && vs > 0) {
                     // the job's epilogue adds to Sigma: bring those lines to L2 while the job runs
                     constexpr int kLines = (kCh * (int)sizeof(CT) + 127) / 128;
@@ -1272,112 +1415,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         if (E < d.ne)
                             prefetch_l2((const uint8_t *)(S + (((size_t)k * d.ne + E) * d.na + a) * kCh) + ln * 128);
                     }
-                }
-
-                if (slot_first) {
-                    // Slot tables: dH (fp32, padded), the direct Toeplitz table of the folded,
-                    // split, k-rotated Dt, and the pre-product's dH operand.  No MMA reads
-                    // them now: the previous job's MMAs are complete.
-                    const int b = s_slot[vs];
-                    const CT *dh = dH + ((size_t)a * d.nb + b) * 3 * kCh;
-                    for (int x = tid; x < 3 * kCh; x += kTcBuilders)
-                        sDh[dh_at(x / kCh, (x % kCh) / 12, x % 12)] = load_c32(dh + x);
-                    float2 *dfold = (float2 *)sB;  // [kappa][w][ij] folded Dt, B stages as scratch
-                    for (int x = tid; x < NK * nw * 9; x += kTcBuilders) {
-                        const int ij = x % 9, w = (x / 9) % nw, kap = x / (9 * nw);
-                        float2 acc = make_float2(0.f, 0.f);
-                        for (int q = kap; q < d.nqz; q += NK) {
-                            const float2 v = load_c32(D + ((((size_t)q * nw + w) * d.na + a) * d.nb + b) * 9 + ij);
-                            acc.x += v.x;
-                            acc.y += v.y;
-                        }
-                        dfold[x] = acc;
-                    }
-                    builders_sync();
-                    const int nitems = 2 * 2 * GG::DA_GROUPS * 2 * da_rows / 2;
-                    for (int x = tid; x < nitems; x += kTcBuilders) {
-                        const int r = x % da_rows, kg = (x / da_rows) % 2, gq = (x / (2 * da_rows)) % GG::DA_GROUPS;
-                        const int q = x / (2 * da_rows * GG::DA_GROUPS);
-                        const int k = gq / 3, j = gq % 3, w0 = r - (GG::DA_TE - 1);
-                        float v[8];
-#pragma unroll
-                        for (int xx = 0; xx < 8; ++xx) {
-                            const int kk = kg * 8 + xx;
-                            float val = 0.f;
-                            if (gq < 3 * NK && kk < 3 * NK && w0 >= 0 && w0 < nw) {
-                                const int i = kk / NK, kp = kk % NK;
-                                const float2 T = dfold[(((k - kp + NK) % NK) * nw + w0) * 9 + i * 3 + j];
-                                val = q ? T.y : T.x;
-                            }
-                            v[xx] = val;
-                        }
-                        uint32_t hv[4], lv[4];
-#pragma unroll
-                        for (int xx = 0; xx < 4; ++xx) {
-                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
-                            hv[xx] = hl.x;
-                            lv[xx] = hl.y;
-                        }
-                        const size_t base_hi = ((((size_t)(q * 2 + 0) * GG::DA_GROUPS + gq) * 2 + kg) * da_rows + r) * 16;
-                        const size_t base_lo = ((((size_t)(q * 2 + 1) * GG::DA_GROUPS + gq) * 2 + kg) * da_rows + r) * 16;
-                        *(uint4 *)(sTab + base_hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *(uint4 *)(sTab + base_lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-                    }
-                    // A_pre[(i, r, re/im), (pc, u)]: the complex product dH_i . G as a real one
-                    // (row re: (Re dH, -Im dH); row im: (Im dH, Re dH))
-                    for (int x = tid; x < kRowsMax * 4; x += kTcBuilders) {
-                        const int m = x >> 2, kg = x & 3;
-                        float v[8];
-#pragma unroll
-                        for (int xx = 0; xx < 8; ++xx) {
-                            const int kk = kg * 8 + xx;
-                            float val = 0.f;
-                            if (m < 72 && kk < 24) {
-                                const int pr = m & 1, r = (m >> 1) % 12, i = (m >> 1) / 12, pc = kk / 12, u = kk % 12;
-                                const float2 h = sDh[dh_at(i, r, u)];
-                                val = pr ? (pc ? h.x : h.y) : (pc ? -h.y : h.x);
-                            }
-                            v[xx] = val;
-                        }
-                        uint32_t hv[4], lv[4];
-#pragma unroll
-                        for (int xx = 0; xx < 4; ++xx) {
-                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
-                            hv[xx] = hl.x;
-                            lv[xx] = hl.y;
-                        }
-                        uint8_t *dst = sApre + (m >> 3) * 512 + kg * 128 + (m & 7) * 16;
-                        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *(uint4 *)(dst + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-                    }
-                    // post-product B[(s, c'), (j, t, c)]: V conj(H) = (Vr Hr + Vi Hi) + i (Vi Hr - Vr Hi)
-                    for (int x = tid; x < 32 * kPostKc; x += kTcBuilders) {
-                        const int row = x / kPostKc, kc = x % kPostKc, s2 = row >> 1, cp = row & 1;
-                        float v[8];
-#pragma unroll
-                        for (int xx = 0; xx < 8; ++xx) {
-                            const int kk = kc * 8 + xx;
-                            float val = 0.f;
-                            if (row < 24 && kk < 72) {
-                                const int j = kk / 24, t = (kk % 24) >> 1, c = kk & 1;
-                                const float2 h = sDh[dh_at(j, s2, t)];
-                                val = cp ? (c ? h.x : -h.y) : (c ? h.y : h.x);
-                            }
-                            v[xx] = val;
-                        }
-                        uint32_t hv[4], lv[4];
-#pragma unroll
-                        for (int xx = 0; xx < 4; ++xx) {
-                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
-                            hv[xx] = hl.x;
-                            lv[xx] = hl.y;
-                        }
-                        uint8_t *dst = sBpost + (row >> 3) * kPostSbo + kc * 128 + (row & 7) * 16;
-                        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *(uint4 *)(dst + kPostBPlane) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-                    }
-                    fence_proxy_async_smem();
-                    mbar_arrive(bar_slot);
                 }
 
                 // ---- X of this stage: TMEM rows (i, r, re/im) -> sX ----
@@ -1450,7 +1487,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     ++job_ctr;
                     tc_fence_after();
                     builders_sync();  // every builder is done with X and B before the A tile overlays them
-                    const bool first_slot = vs == 0;
+                    const bool first_slot = vs == 0, last_slot = vs == nvalid - 1;
                     // A-tile role: warp -> (lane quarter, row r' of the tile); lane -> accumulator row
                     const int aq = warp & 3, arl = warp >> 2;
                     const int am = aq * 32 + lane;
@@ -1460,7 +1497,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const int drow = dq * 32 + lane;  // tile row (r', e, k)
                     const int drl = drow / 40, de = (drow / 5) % 8, dk = drow % 5;
                     const bool dlive = drow < 120 && E0 + de < d.ne;
-                    CT old[4];
+                    float2 old[4];
                     CT *dst = S;
                     // Tile q: its A is built once the MMAs of tile q - 1 are done (one A buffer);
                     // the accumulator columns it needs are loaded before that wait, and the FP64
@@ -1521,8 +1558,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         }
                         if (q > 0 && dlive) {
 #pragma unroll
-                            for (int s2 = 0; s2 < 4; ++s2)
-                                dst[s2] = slot_sum<CT>(make_float2(pv[2 * s2], pv[2 * s2 + 1]), old[s2], first_slot);
+                            for (int s2 = 0; s2 < 4; ++s2) {
+                                const float2 v = make_float2(pv[2 * s2] + old[s2].x, pv[2 * s2 + 1] + old[s2].y);
+                                if (last_slot) dst[s2] = final_of<CT>(v);
+                                else *partial_of(dst + s2) = v;
+                            }
                         }
                         if (q < 4) {
                             // the slots summed so far for the rows this thread takes from tile q
@@ -1530,9 +1570,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                                   4 * dsub;
 #pragma unroll
                             for (int s2 = 0; s2 < 4; ++s2) {
-                                old[s2].x = 0;
-                                old[s2].y = 0;
-                                if (dlive && !first_slot) old[s2] = dst[s2];
+                                old[s2] = make_float2(0.f, 0.f);
+                                if (dlive && !first_slot) old[s2] = *partial_of(dst + s2);
                             }
                         }
                     }
@@ -1558,6 +1597,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (abort && prd && lane == 0) {
         for (int b = 0; b < kTcRing; ++b)
             if (last_g[b] >= 0) mbar_wait_bounded(&bar_g[b], (last_g[b] / kTcRing) & 1, kWaitNs);
+        if (slot_cp > 0) mbar_wait_bounded(bar_slot, (slot_cp - 1) & 1, kWaitNs);
     }
     tc_fence_before();
     __syncthreads();
@@ -1584,11 +1624,10 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
     prm.off_a = take(2 * 8192, 1024);
     const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
     prm.off_df = take(2u * 2u * GG::DA_GROUPS * 2u * rows * 16u, 1024);
-    prm.off_dh = take(3 * kDhJ * 8, 16);
+    prm.off_dh = 0;
     prm.off_bp = take(2 * kPostBPlane, 1024);
     prm.off_bar = take(kTcBarBytes + 8 + 2 * kMaxSlots * 4, 8);
     prm.g_stage = 0;
-    if ((uint32_t)(5 * d.nw * 9 * 8) > bsz) return 0xFFFFFFFFu;
     return off;
 }
 
@@ -1668,9 +1707,12 @@ bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc) {
     I.ntiles = (I.ne + GG::TE - 1) / GG::TE;
     I.tiles_per_cta = tpc < 1 ? 1 : (tpc > I.ntiles ? I.ntiles : tpc);
     const size_t sign_bytes = ((size_t)p.d.ne * p.d.na + 1) * 8192;
+    const size_t tab_sign = (size_t)p.d.na * p.d.nb * tc_entry_bytes(p.d.nw);
     const uint8_t *ws = (const uint8_t *)p.mixed_ws;
     I.gws[0] = ws ? ws + (do_gt ? 0 : sign_bytes) : nullptr;
     I.gws[1] = ws ? ws + sign_bytes : nullptr;
+    I.sws[0] = ws ? ws + 2 * sign_bytes + (do_gt ? 0 : tab_sign) : nullptr;
+    I.sws[1] = ws ? ws + 2 * sign_bytes + tab_sign : nullptr;
     I.nchunks = (I.ntiles + I.tiles_per_cta - 1) / I.tiles_per_cta;
     return true;
 }
@@ -1700,20 +1742,29 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
     return SSE_OK;
 }
 
-// Re-encode the G of every requested sign of one instance into its plan's workspace.
+// Fill the plan's workspace for every requested sign of one instance: G re-encoded for the
+// pre-product and the slot tables.
 template <typename CT>
 sse_status split_g(const Plan &p, const sse_io &io, cudaStream_t st) {
     const size_t sign_bytes = ((size_t)p.d.ne * p.d.na + 1) * 8192;
+    const size_t tab_sign = (size_t)p.d.na * p.d.nb * tc_entry_bytes(p.d.nw);
     const void *gs[2] = {io.S_gt ? io.G_gt : nullptr, io.S_lt ? io.G_lt : nullptr};
+    const void *ds[2] = {io.D_gt, io.D_lt};
+    const uint32_t tsmem = 3 * kDhJ * 8 + 5 * p.d.nw * 9 * 8;
     for (int s = 0; s < 2; ++s) {
         if (!gs[s]) continue;
         const long long slices = (long long)p.d.ne * p.d.na;
-        if (slices > 0x7fffffffLL) return set_error("mixed mode: too many G slices"), SSE_E_INVALID_ARG;
-        sse_split_g_kernel<CT><<<(unsigned)slices, 256, 0, st>>>((const CT *)gs[s], (uint8_t *)p.mixed_ws + s * sign_bytes,
-                                                                p.d.ne, p.d.na, p.d.nkz);
+        if (slices > 0x7fffffffLL || (long long)p.d.na * p.d.nb > 0x7fffffffLL)
+            return set_error("mixed mode: instance too large"), SSE_E_INVALID_ARG;
+        uint8_t *ws = (uint8_t *)p.mixed_ws;
+        sse_split_g_kernel<CT><<<(unsigned)slices, 256, 0, st>>>((const CT *)gs[s], ws + s * sign_bytes, p.d.ne,
+                                                                p.d.na, p.d.nkz);
+        sse_slot_tables_kernel<CT><<<(unsigned)(p.d.na * p.d.nb), 256, tsmem, st>>>(
+            (const CT *)ds[s], (const CT *)p.geo.dH, p.geo.neigh, ws + 2 * sign_bytes + s * tab_sign, p.d.na, p.d.nb,
+            p.d.nqz, p.d.nw);
     }
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "launch sse_split_g_kernel");
+    if (e != cudaSuccess) return cuda_fail(e, "launch the workspace kernels");
     return SSE_OK;
 }
 
@@ -1871,16 +1922,19 @@ sse_status mixed_plan_init(Plan &p) {
     // Nkz = 5: the warp-specialised tensor-core form when its tiles fit (Nw <= 40), with a
     // workspace; otherwise the direct form above
     if (d.nkz == 5 && tc_smem_bytes(d, prm) <= 232448u) {
-        // workspace of the tensor-core pre-product: G re-encoded per sign, plus a zero slice
+        // workspace of the tensor-core form, per sign: G re-encoded for the pre-product plus a
+        // zero slice, then the slot tables of every (atom, slot)
         const size_t sign_bytes = ((size_t)d.ne * d.na + 1) * 8192;
-        cudaError_t e = cudaMalloc(&p.mixed_ws, 2 * sign_bytes);
+        const size_t tab_sign = (size_t)d.na * d.nb * tc_entry_bytes(d.nw);
+        const size_t bytes = 2 * sign_bytes + 2 * tab_sign;
+        cudaError_t e = cudaMalloc(&p.mixed_ws, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             p.mixed_ws = nullptr;
-            set_error("cudaMalloc of %zu bytes for the mixed workspace failed", 2 * sign_bytes);
+            set_error("cudaMalloc of %zu bytes for the mixed workspace failed", bytes);
             return SSE_E_OUT_OF_MEMORY;
         }
-        p.mixed_ws_bytes = 2 * sign_bytes;
+        p.mixed_ws_bytes = bytes;
         p.workspace_bytes += (int64_t)p.mixed_ws_bytes;
         for (int s2 = 0; s2 < 2; ++s2) {
             e = cudaMemset((uint8_t *)p.mixed_ws + s2 * sign_bytes + (size_t)d.ne * d.na * 8192, 0, 8192);
