@@ -186,6 +186,17 @@ SSE_API sse_status sse_server_stats(sse_server_t *server, uint64_t *rounds, uint
  * its kernels write: SSE_OK, or SSE_E_TIMEOUT if a bounded device wait expired. */
 SSE_API sse_status sse_plan_status(sse_plan_t *plan);
 
+/* Kernel timing of sse_execute on one plan, for benchmarks and profiling; the paper has no
+ * counterpart.  While enabled, every sse_execute call on the plan records three CUDA events
+ * on its stream: before the workspace pass (the Nkz = 5 tensor-core form re-encodes G and
+ * builds the slot tables there; other forms have none), before the main kernel and after
+ * it.  enable != 0 starts timing and zeroes the totals (the first call creates the events);
+ * 0 stops.  Batched and served executions are not timed. */
+SSE_API sse_status sse_plan_set_timing(sse_plan_t *plan, int32_t enable);
+/* Totals since timing was enabled: milliseconds spent in the workspace pass and in the
+ * main kernel over `calls` timed calls.  Waits for the recorded events. */
+SSE_API sse_status sse_plan_timing(sse_plan_t *plan, double *prep_ms, double *main_ms, int64_t *calls);
+
 /* Mixed-mode evaluation for callers that cannot let this library allocate memory (for
  * example a framework whose allocator owns all device memory, or a loop that must not
  * stall on cudaMalloc/cudaFree).  No plan is created and nothing is allocated: the

@@ -99,6 +99,39 @@ double plan_slots_per_atom(const sse_plan_t *p) { return p->slots_per_atom; }
 sse_status plan_check_io(sse_plan_t *p, const sse_io *io) { return check_io(*p, io); }
 }  // namespace sse
 
+namespace sse {
+namespace {
+void timing_accumulate(KernelTiming &t, int slot) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventSynchronize(t.ev[slot][2]) == cudaSuccess && cudaEventElapsedTime(&a, t.ev[slot][0], t.ev[slot][1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, t.ev[slot][1], t.ev[slot][2]) == cudaSuccess) {
+        t.prep_ms += a;
+        t.main_ms += b;
+    }
+    cudaGetLastError();
+    ++t.done;
+}
+void timing_free(KernelTiming &t) {
+    for (auto &tr : t.ev)
+        for (auto &e : tr)
+            if (e) cudaEventDestroy(e), e = nullptr;
+}
+}  // namespace
+
+int timing_slot(Plan &p) {
+    KernelTiming &t = p.timing;
+    if (!t.on) return -1;
+    const int slot = (int)(t.issued % KernelTiming::kRing);
+    if (t.issued - t.done >= KernelTiming::kRing) timing_accumulate(t, slot);
+    ++t.issued;
+    return slot;
+}
+
+void timing_mark(Plan &p, int slot, int which, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(p.timing.ev[slot][which], st);
+}
+}  // namespace sse
+
 extern "C" {
 
 int32_t sse_abi_version(void) { return 1; }
@@ -186,6 +219,7 @@ sse_status sse_plan_destroy(sse_plan_t *plan) {
     if (!plan) return SSE_OK;
     if (plan->last_stream) cudaStreamSynchronize(plan->last_stream);
     mixed_plan_free(*plan);
+    timing_free(plan->timing);
     if (plan->d_status) cudaFree(plan->d_status);
     if (plan->staging) cudaFree(plan->staging);
     delete plan;
@@ -207,10 +241,16 @@ sse_status sse_plan_query(const sse_plan_t *plan, sse_plan_info *info) {
     return SSE_OK;
 }
 
+
 static sse_status dispatch(sse_plan_t *plan, const sse_io &io, cudaStream_t st) {
     plan->last_stream = st;
     if (plan->kernel_id == 1) return launch_mixed(*plan, io, st);
-    return launch_fp64_direct(*plan, io, st);
+    const int ts = timing_slot(*plan);
+    timing_mark(*plan, ts, 0, st);
+    timing_mark(*plan, ts, 1, st);
+    const sse_status rs = launch_fp64_direct(*plan, io, st);
+    timing_mark(*plan, ts, 2, st);
+    return rs;
 }
 
 sse_status sse_execute(sse_plan_t *plan, const sse_io *io, void *stream) {
@@ -309,6 +349,33 @@ sse_status sse_batch_tuning(sse_plan_t *const *plans, const sse_io *ios, int32_t
     if (!batch_choice(ps.data(), ios, n, &tpc, &lpt)) return SSE_NOT_READY;
     *tiles_per_unit = tpc;
     *longest_first = lpt;
+    return SSE_OK;
+}
+
+sse_status sse_plan_set_timing(sse_plan_t *plan, int32_t enable) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    KernelTiming &t = plan->timing;
+    if (enable) {
+        for (auto &tr : t.ev)
+            for (auto &e : tr)
+                if (!e) {
+                    cudaError_t err = cudaEventCreate(&e);
+                    if (err != cudaSuccess) return cuda_fail(err, "cudaEventCreate(timing)");
+                }
+    }
+    t.on = enable != 0;
+    t.issued = t.done = 0;
+    t.prep_ms = t.main_ms = 0.0;
+    return SSE_OK;
+}
+
+sse_status sse_plan_timing(sse_plan_t *plan, double *prep_ms, double *main_ms, int64_t *calls) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    KernelTiming &t = plan->timing;
+    while (t.done < t.issued) timing_accumulate(t, (int)(t.done % KernelTiming::kRing));
+    if (prep_ms) *prep_ms = t.prep_ms;
+    if (main_ms) *main_ms = t.main_ms;
+    if (calls) *calls = t.done;
     return SSE_OK;
 }
 

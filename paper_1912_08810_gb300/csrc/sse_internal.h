@@ -21,6 +21,16 @@ struct Dims {
     int32_t nkz, nqz, ne, nw, na, nb, omega_first;
 };
 
+// Event timing of sse_execute (sse_plan_set_timing): a ring of (start, after the workspace
+// pass, after the main kernel) event triples, accumulated when a slot is reused or on query.
+struct KernelTiming {
+    static constexpr int kRing = 64;
+    bool on = false;
+    cudaEvent_t ev[kRing][3] = {};
+    int64_t issued = 0, done = 0;
+    double prep_ms = 0.0, main_ms = 0.0;
+};
+
 struct Plan {
     sse_geometry geo{};
     Dims d{};
@@ -32,11 +42,18 @@ struct Plan {
     size_t staging_bytes = 0;
     cudaStream_t last_stream = nullptr;
     int64_t workspace_bytes = 0;
-    // Mixed-path workspace (see sse_mixed.cu): G of each sign re-encoded as bf16 hi/lo
-    // slices in tensor-core operand layout, (ne * na + 1) slices per sign (the last is zero)
+    // Mixed-path workspace (see sse_mixed.cu), Nkz = 5 tensor-core form: per sign, G
+    // re-encoded as bf16 hi/lo slices in operand layout ((ne * na + 1) slices, the last zero),
+    // then the slot tables of every (atom, slot)
     void *mixed_ws = nullptr;
     size_t mixed_ws_bytes = 0;
+    KernelTiming timing;
 };
+
+// Timing hooks: timing_slot returns the ring slot of this call (-1 when timing is off);
+// timing_mark records event `which` (0 start, 1 after the workspace pass, 2 end) on `st`.
+int timing_slot(Plan &p);
+void timing_mark(Plan &p, int slot, int which, cudaStream_t st);
 
 // Thread-local error message for sse_last_error().
 void set_error(const char *fmt, ...);

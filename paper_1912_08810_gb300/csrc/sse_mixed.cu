@@ -1793,14 +1793,18 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     prm.total_units = inst_units(prm.inst[0]);
     prm.queue = nullptr;
     if (prm.total_units > 0x7fffffffLL) return set_error("mixed mode: grid too large"), SSE_E_INVALID_ARG;
+    const int ts = timing_slot(p);
+    timing_mark(p, ts, 0, st);
     if (V3) {
         rs = split_g<CT>(p, io, st);
         if (rs != SSE_OK) return rs;
     }
+    timing_mark(p, ts, 1, st);
     if constexpr (V3)
         sse_tc_kernel<CT><<<(unsigned)prm.total_units, kTcThreads, smem, st>>>(prm);
     else
         sse_mixed_kernel<NK, CT, false><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
+    timing_mark(p, ts, 2, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch sse_mixed_kernel");
     p.tile_e = GG::TE;

@@ -39,6 +39,7 @@ EXPORTED = (
     "sse_plan_status", "sse_status_string", "sse_last_error", "sse_abi_version",
     "sse_execute_noalloc", "sse_execute_batch", "sse_batch_tuning",
     "sse_server_create", "sse_submit", "sse_poll", "sse_server_destroy", "sse_server_stats",
+    "sse_plan_set_timing", "sse_plan_timing",
 )
 
 
@@ -109,6 +110,9 @@ def load(path: Optional[str] = None):
             "sse_server_destroy": ([vp], st),
             "sse_server_stats": ([vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                   ctypes.POINTER(ctypes.c_int32)], st),
+            "sse_plan_set_timing": ([vp, ctypes.c_int32], st),
+            "sse_plan_timing": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int64)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -160,6 +164,17 @@ def sse_execute_host(plan, io: sse_io, stream: int = 0) -> None:
 
 def sse_plan_status(plan) -> None:
     _check(load().sse_plan_status(plan), "sse_plan_status")
+
+
+def sse_plan_set_timing(plan, enable: bool) -> None:
+    _check(load().sse_plan_set_timing(plan, ctypes.c_int32(1 if enable else 0)), "sse_plan_set_timing")
+
+
+def sse_plan_timing(plan):
+    """(workspace-pass ms, main-kernel ms, timed calls) since timing was enabled."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(load().sse_plan_timing(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)), "sse_plan_timing")
+    return a.value, b.value, n.value
 
 
 def sse_execute_noalloc(geo: sse_geometry, io: sse_io, stream: int = 0) -> None:
