@@ -951,14 +951,19 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // control -> builders through MMA commits ("X of stage g ready", "job accumulated").  A
 // third role, one more warp, streams the G slices into a ring of four; the control warp
 // hands a ring slot back with an MMA commit once the pre-product that read it is done.
-// The pre-product of stage g + 2 is issued as soon as B of stage g is ready (the builders
-// have drained its TMEM buffer by then), ahead of stage g's main MMAs, so the builders never
-// wait for X while the tensor pipe has work.  The product with dH_j^dagger at the end of a
+// The pre-product runs for two stages at once (N = 128: the two G slices side by side), as
+// soon as the builders have drained the previous pair (at its first stage), ahead of the
+// main MMAs, so the builders rarely wait for X while the tensor pipe has work.  The product with dH_j^dagger at the end of a
 // job runs on the tensor cores too: the builders re-encode the accumulators tile by tile
 // (bf16 hi / lo, three products as elsewhere) and the control warp issues its MMAs.
 constexpr int kTcBuilders = 384;
 constexpr int kTcThreads = kTcBuilders + 64;  // + control warp + bulk-copy warp
-constexpr int kTcRing = 4;   // G slices in flight
+constexpr int kTcRing = 2;   // pairs of G slices in flight
+constexpr uint32_t kTcPairBytes = 16384;  // one ring slot: two slices, [hi s0 | hi s1 | lo s0 | lo s1]
+// TMEM columns of the warp-specialised kernel
+constexpr uint32_t kTcAccIm = 160;             // Im V (Re V at 0), 144 columns each
+constexpr uint32_t kTcPost0 = 320, kTcPost1 = 352;  // post-product accumulators, 32 columns each
+constexpr uint32_t kTcPre = 384;               // X of a pair of stages, 2 x 64 columns
 constexpr int kDhJ = 160;    // float2 per direction j of the padded dH copy
 constexpr int kXs = 76;      // row stride (floats) of the X buffer
 // Post-product Sigma_slot[(e, k), r, s] = sum_{j, t} V_j[(e, k)][r, t] conj(dH_j[s, t]) on the
@@ -968,7 +973,6 @@ constexpr int kPostK = 80, kPostKc = kPostK / 8;            // K and its 16-byte
 constexpr uint32_t kPostSbo = kPostKc * 128;                // bytes between 8-row groups
 constexpr uint32_t kPostAPlane = (kRowsMax / 8) * kPostSbo;  // 20480
 constexpr uint32_t kPostBPlane = (32 / 8) * kPostSbo;        // 5120
-constexpr uint32_t kPostCol0 = 160, kPostCol1 = 416;        // post-product accumulators (32 columns)
 constexpr int kTcBarBytes = 192;  // 20 mbarriers, the TMEM address and the flags; the unit index follows
 
 // Row of the X buffer that holds pre-product row m = (i, r, re/im): rows ordered
@@ -1121,23 +1125,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     float *sX = (float *)(smem + prm.off_x);     // X rows (i, r, re/im) x (k', t)
     uint8_t *sApost = smem + prm.off_b;          // epilogue: post-product A tile over the B stages and X
     uint8_t *sBpost = smem + prm.off_bp;         // post-product B of the slot: conj(dH_j) [hi, lo]
-    uint8_t *sRing = smem + prm.off_g;           // [kTcRing] re-encoded G slices
+    uint8_t *sRing = smem + prm.off_g;           // [kTcRing] pairs of re-encoded G slices
     uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
     uint8_t *sTab = smem + prm.off_df;           // direct Toeplitz table of the slot
     uint64_t *bars = (uint64_t *)(smem + prm.off_bar);
-    uint64_t *bar_g = bars;                      // [kTcRing] slice landed
-    uint64_t *bar_pre = bars + kTcRing;          // [2] pre-product of a stage done
-    uint64_t *bar_bready = bars + kTcRing + 2;   // [2] B of a stage built
-    uint64_t *bar_job = bars + kTcRing + 4;      // last MMAs of a job done
-    uint64_t *bar_slot = bars + kTcRing + 5;     // slot tables copied in
-    uint64_t *bar_fin = bars + kTcRing + 6;      // abort: every MMA issued so far done
-    uint64_t *bar_mma = bars + kTcRing + 7;      // [2] main MMAs of a stage done (B buffer free)
-    uint64_t *bar_apost = bars + kTcRing + 9;    // post-product A tile built
-    uint64_t *bar_post = bars + kTcRing + 10;    // [2] post-product MMAs of a tile done
-    uint64_t *bar_empty = bars + kTcRing + 12;   // [kTcRing] pre-product done with a ring slot
-    uint64_t *bar_slotfree = bars + 2 * kTcRing + 12;  // every MMA of the previous slot done
-    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 13);
-    static_assert((2 * kTcRing + 13) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
+    uint64_t *bar_g = bars;                      // [kTcRing] pair of slices landed
+    uint64_t *bar_pre = bars + kTcRing;          // pre-product of a pair done
+    uint64_t *bar_bready = bars + kTcRing + 1;   // [2] B of a stage built
+    uint64_t *bar_job = bars + kTcRing + 3;      // last MMAs of a job done
+    uint64_t *bar_slot = bars + kTcRing + 4;     // slot tables copied in
+    uint64_t *bar_fin = bars + kTcRing + 5;      // abort: every MMA issued so far done
+    uint64_t *bar_mma = bars + kTcRing + 6;      // [2] main MMAs of a stage done (B buffer free)
+    uint64_t *bar_apost = bars + kTcRing + 8;    // post-product A tile built
+    uint64_t *bar_post = bars + kTcRing + 9;     // [2] post-product MMAs of a tile done
+    uint64_t *bar_empty = bars + kTcRing + 11;   // [kTcRing] pre-product done with a ring slot
+    uint64_t *bar_slotfree = bars + 2 * kTcRing + 11;  // every MMA of the previous slot done
+    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 12);
+    static_assert((2 * kTcRing + 12) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
     // abort flags: builders write slot g & 1 during stage g and all read it after the stage's
     // last barrier (the next write to that slot comes after another barrier); the control
     // warp has its own flag
@@ -1151,8 +1155,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 
     if (tid == 0) {
         for (int b = 0; b < kTcRing; ++b) mbar_init(&bar_g[b], 1);
-        mbar_init(&bar_pre[0], 1);
-        mbar_init(&bar_pre[1], 1);
+        mbar_init(bar_pre, 1);
         mbar_init(&bar_bready[0], kTcBuilders);
         mbar_init(&bar_bready[1], kTcBuilders);
         mbar_init(bar_job, 1);
@@ -1180,8 +1183,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    int last_g[kTcRing];  // bulk-copy lane 0: last stage copied into each ring slot
+    int last_g[kTcRing];  // bulk-copy lane 0: last pair copied into each ring slot
     int slot_cp = 0;      // bulk-copy lane 0: slot tables copied so far
+    int pair_ctr = 0;     // pairs of stages so far (each role keeps its own count)
 #pragma unroll
     for (int b = 0; b < kTcRing; ++b) last_g[b] = -1;
     int g_base = 0, job_ctr = 0, slot_ctr = 0;
@@ -1257,14 +1261,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 // descriptors: fixed parts built once; a shift of the start address is an add
                 // on the descriptor's low field (shared addresses stay below 2^18)
                 const uint64_t pa_h0 = smem_desc(smem_u32(sApre), 128, 512), pa_l0 = smem_desc(smem_u32(sApre) + 8192, 128, 512);
-                const uint64_t pb_h0 = smem_desc(smem_u32(sRing), 128, 512), pb_l0 = smem_desc(smem_u32(sRing) + 4096, 128, 512);
-                auto premma = [&](int g) -> bool {
-                    const int gg = g_base + g, slot = gg % kTcRing;
-                    if (!mbar_wait_bounded(&bar_g[slot], (gg / kTcRing) & 1, kWaitNs)) return false;
+                const uint64_t pb_h0 = smem_desc(smem_u32(sRing), 128, 512), pb_l0 = smem_desc(smem_u32(sRing) + 8192, 128, 512);
+                // pre-product of the next pair of stages: rows (i, r, re/im), N = (stage of the
+                // pair, k', t) = 128, K = (re/im of G, u)
+                auto premma = [&]() -> bool {
+                    const int slot = pair_ctr % kTcRing;
+                    if (!mbar_wait_bounded(&bar_g[slot], (pair_ctr / kTcRing) & 1, kWaitNs)) return false;
                     tc_fence_after();
-                    constexpr uint32_t idesc_x = idesc_bf16_f32(kRowsMax, GG::XP_N);
-                    const uint64_t boff = (uint64_t)((slot * GG::XP_SLICE) >> 4);
-                    const uint32_t dx = tmem + ((gg & 1) ? kPreCol1 : kPreCol0);
+                    constexpr uint32_t idesc_x = idesc_bf16_f32(kRowsMax, 128);
+                    const uint64_t boff = (uint64_t)((slot * kTcPairBytes) >> 4);
+                    const uint32_t dx = tmem + kTcPre;
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint64_t ko = (uint64_t)(ks * 256 >> 4);
@@ -1272,8 +1278,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         mma_ss(dx, pa_h0 + ko, pb_l0 + boff + ko, idesc_x, 1u);
                         mma_ss(dx, pa_l0 + ko, pb_h0 + boff + ko, idesc_x, 1u);
                     }
-                    mma_commit(&bar_pre[gg & 1]);
+                    mma_commit(bar_pre);
                     mma_commit(&bar_empty[slot]);  // the ring slot can be refilled
+                    ++pair_ctr;
                     return true;
                 };
                 Pos m{t_begin, 0, 0};
@@ -1293,33 +1300,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 const uint64_t pp_al = smem_desc(smem_u32(sApost) + kPostAPlane, 128, kPostSbo);
                 const uint64_t pp_bh = smem_desc(smem_u32(sBpost), 128, kPostSbo);
                 const uint64_t pp_bl = smem_desc(smem_u32(sBpost) + kPostBPlane, 128, kPostSbo);
-                const int ntl = t_end - t_begin;
+                const int slot_len = (t_end - t_begin) * prm.nst;  // stages of one slot in this unit
                 bool ok = true;
-                for (int g = 0; g < total; ++g, advance(m)) {
+                int o = 0;  // stage index within the slot
+                for (int g = 0; g < total; ++g, advance(m), o = (o + 1 == slot_len) ? 0 : o + 1) {
                     const int gg = g_base + g;
                     const bool job_first = m.st == 0, job_last = m.st == prm.nst - 1;
-                    const bool slot_first = job_first && m.t == t_begin;
-                    // stages after this one that still belong to its slot
-                    const int slot_rem = (t_begin + ntl - 1 - m.t) * prm.nst + (prm.nst - 1 - m.st);
-                    if (slot_first) {
+                    const int slot_rem = slot_len - 1 - o;  // stages after this one in its slot
+                    if (o == 0) {
                         ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs);
                         ++slot_ctr;
                         if (!ok) break;
                         tc_fence_after();
-                        if (!(ok = premma(g))) break;
-                        if (slot_rem >= 1 && !(ok = premma(g + 1))) break;
+                        if (!(ok = premma())) break;
                     }
                     if (!(ok = mbar_wait_bounded(&bar_bready[gg & 1], (gg >> 1) & 1, kWaitNs))) break;
                     tc_fence_after();
-                    // X of stage g + 2 ahead of this stage's main MMAs: its TMEM buffer was drained
-                    // in stage g, and its G slice was requested two stages ago
-                    if (slot_rem >= 2 && !(ok = premma(g + 2))) break;
+                    // X of the next pair ahead of this stage's main MMAs: the builders drained the
+                    // TMEM buffer at this (first) stage of the current pair
+                    if ((o & 1) == 0 && slot_rem >= 2 && !(ok = premma())) break;
                     const uint64_t r_start = (uint64_t)(nw - 1 - m.st + GG::DA_TE - 1);
                     const uint64_t are_h = ta[0] + r_start, are_l = ta[1] + r_start;
                     const uint64_t aim_h = ta[2] + r_start, aim_l = ta[3] + r_start;
                     const int bb = gg & 1;
                     const uint64_t bre_h = tb[bb][0], bre_l = tb[bb][1], bim_h = tb[bb][2], bim_l = tb[bb][3];
-                    const uint32_t dre = tmem, dim = tmem + kAccIm;
+                    const uint32_t dre = tmem, dim = tmem + kTcAccIm;
                     const uint32_t acc0 = job_first ? 0u : 1u;
                     // Re V = Re T Re X - Im T Im X
                     mma_ss(dre, are_h, bre_h, idesc, acc0);
@@ -1343,7 +1348,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         for (int q = 0; q < 4 && ok; ++q, ++tile_ctr) {
                             if (!(ok = mbar_wait_bounded(bar_apost, tile_ctr & 1, kWaitNs))) break;
                             tc_fence_after();
-                            const uint32_t dp = tmem + ((tile_ctr & 1) ? kPostCol1 : kPostCol0);
+                            const uint32_t dp = tmem + ((tile_ctr & 1) ? kTcPost1 : kTcPost0);
 #pragma unroll
                             for (int ks = 0; ks < kPostK / 16; ++ks) {
                                 const uint64_t ko = (uint64_t)(ks * 256 >> 4);
@@ -1368,30 +1373,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             if (lane == 0) {
                 const uint8_t *gws = I.gws[sign];
                 const uint32_t tbytes = tc_table_bytes(nw), ebytes = tc_entry_bytes(nw);
-                Pos pf{t_begin, 0, 0};
+                const int slot_len = (t_end - t_begin) * prm.nst;
+                const long long zero = (long long)d.ne * d.na;  // the zero slice
                 bool ok = true;
-                for (int g = 0; g < total; ++g, advance(pf)) {
-                    const int gg = g_base + g, slot = gg % kTcRing, use = gg / kTcRing;
-                    if (pf.st == 0 && pf.t == t_begin) {
-                        // a new slot: its tables replace the previous slot's once every MMA that
-                        // read those is done (the CTA's first slot: nothing to wait for)
-                        if (!(ok = mbar_wait_bounded(bar_slotfree, (slot_cp & 1) ^ 1, kWaitNs))) break;
-                        const uint8_t *src = I.sws[sign] + ((size_t)a * d.nb + s_slot[pf.vs]) * ebytes;
-                        mbar_arrive_expect_tx(bar_slot, ebytes);
-                        bulk_g2s(sTab, src, tbytes, bar_slot);
-                        bulk_g2s(sApre, src + tbytes, 16384, bar_slot);
-                        bulk_g2s(sBpost, src + tbytes + 16384, 2 * kPostBPlane, bar_slot);
-                        ++slot_cp;
+                for (int vs = 0; vs < nvalid && ok; ++vs) {
+                    // a new slot: its tables replace the previous slot's once every MMA that read
+                    // those is done (the CTA's first slot: nothing to wait for)
+                    if (!(ok = mbar_wait_bounded(bar_slotfree, (slot_cp & 1) ^ 1, kWaitNs))) break;
+                    const uint8_t *src = I.sws[sign] + ((size_t)a * d.nb + s_slot[vs]) * ebytes;
+                    mbar_arrive_expect_tx(bar_slot, ebytes);
+                    bulk_g2s(sTab, src, tbytes, bar_slot);
+                    bulk_g2s(sApre, src + tbytes, 16384, bar_slot);
+                    bulk_g2s(sBpost, src + tbytes + 16384, 2 * kPostBPlane, bar_slot);
+                    ++slot_cp;
+                    const int f = s_f[vs];
+                    for (int o = 0; o < slot_len; o += 2, ++pair_ctr) {
+                        const int slot = pair_ctr % kTcRing, use = pair_ctr / kTcRing;
+                        // ring slot free: the pre-product of its previous pair is done (first use: free)
+                        if (!(ok = mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
+                        mbar_arrive_expect_tx(&bar_g[slot], kTcPairBytes);
+                        uint8_t *dst = sRing + slot * kTcPairBytes;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            // the zero slice stands in for energies below or above the grid and for
+                            // the missing second stage of an odd-length slot
+                            long long slice = zero;
+                            if (o + h < slot_len) {
+                                const int t = t_begin + (o + h) / prm.nst, st = (o + h) % prm.nst;
+                                const int Ep = t * GG::TE - omega_max + st;
+                                if (Ep >= 0 && Ep < d.ne) slice = (long long)Ep * d.na + f;
+                            }
+                            const uint8_t *sl = gws + slice * GG::XP_SLICE;
+                            bulk_g2s(dst + h * 4096, sl, 4096, &bar_g[slot]);
+                            bulk_g2s(dst + 8192 + h * 4096, sl + 4096, 4096, &bar_g[slot]);
+                        }
+                        last_g[slot] = pair_ctr;
                     }
-                    // slot free: the pre-product of its previous stage is done (first use: free)
-                    if (!(ok = mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
-                    // the zero slice stands in for energies below or above the grid
-                    const int Ep = pf.t * GG::TE - omega_max + pf.st;
-                    const long long slice =
-                        (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + s_f[pf.vs] : (long long)d.ne * d.na;
-                    mbar_arrive_expect_tx(&bar_g[slot], GG::XP_SLICE);
-                    bulk_g2s(sRing + slot * GG::XP_SLICE, gws + slice * GG::XP_SLICE, GG::XP_SLICE, &bar_g[slot]);
-                    last_g[slot] = gg;
                 }
                 if (!ok) {
                     *s_abort_prd = 1;
@@ -1402,7 +1419,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         } else {
             // ================= builder warps =================
             Pos cur{t_begin, 0, 0};
-            for (int g = 0; g < total; ++g, advance(cur)) {
+            const int slot_len = (t_end - t_begin) * prm.nst;
+            int o = 0;           // stage index within the slot
+            uint32_t xnext[20];  // drain warps: X of the pair's second stage, kept until then
+            for (int g = 0; g < total; ++g, advance(cur), o = (o + 1 == slot_len) ? 0 : o + 1) {
                 const int t = cur.t, vs = cur.vs, st = cur.st;
                 const int gg = g_base + g, sb = gg & 1;
                 const int E0 = t * GG::TE;
@@ -1417,21 +1437,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     }
                 }
 
-                // ---- X of this stage: TMEM rows (i, r, re/im) -> sX ----
-                if (!mbar_wait_bounded(&bar_pre[sb], (gg >> 1) & 1, kWaitNs)) {
-                    s_abort[sb] = 1;
-                    atomicExch(prm.status, 1);
+                // ---- X of this stage: TMEM rows (i, r, re/im) -> sX; at the first stage of a pair
+                // both stages are drained and the second is kept in registers ----
+                const bool pair_first = (o & 1) == 0;
+                if (pair_first) {
+                    if (!mbar_wait_bounded(bar_pre, pair_ctr & 1, kWaitNs)) {
+                        s_abort[sb] = 1;
+                        atomicExch(prm.status, 1);
+                    }
+                    ++pair_ctr;
+                    tc_fence_after();
                 }
-                tc_fence_after();
                 if ((warp & 3) < 3) {
                     const int cb = warp >> 2;  // 20-column block of the 60 columns (k', t)
-                    const uint32_t taddr =
-                        tmem + ((uint32_t)((warp & 3) * 32) << 16) + (sb ? kPreCol1 : kPreCol0) + 20 * cb;
                     const int m = (warp & 3) * 32 + lane;
                     uint32_t xr[20];
-                    tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(xr));
-                    tmem_ld4(taddr + 16, *reinterpret_cast<uint32_t(*)[4]>(xr + 16));
-                    tmem_ld_wait();
+                    if (pair_first) {
+                        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + kTcPre + 20 * cb;
+                        tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(xr));
+                        tmem_ld4(taddr + 16, *reinterpret_cast<uint32_t(*)[4]>(xr + 16));
+                        tmem_ld16(taddr + 64, *reinterpret_cast<uint32_t(*)[16]>(xnext));
+                        tmem_ld4(taddr + 64 + 16, *reinterpret_cast<uint32_t(*)[4]>(xnext + 16));
+                        tmem_ld_wait();
+                        tc_fence_before();
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < 20; ++x) xr[x] = xnext[x];
+                    }
                     if (m < 72) {
                         float4 *row = (float4 *)(sX + x_row(m) * kXs + 20 * cb);
 #pragma unroll
@@ -1439,7 +1471,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             row[x] = make_float4(__uint_as_float(xr[4 * x]), __uint_as_float(xr[4 * x + 1]),
                                                  __uint_as_float(xr[4 * x + 2]), __uint_as_float(xr[4 * x + 3]));
                     }
-                    tc_fence_before();
                 }
                 builders_sync();
                 // ---- the B buffer must be free: main MMAs of stage g - 2 complete ----
@@ -1509,8 +1540,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             const uint32_t ta = tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)((3 * q + arl) * 12);
                             tmem_ld8(ta, *reinterpret_cast<float(*)[8]>(vr));
                             tmem_ld4(ta + 8, *reinterpret_cast<uint32_t(*)[4]>(vr + 8));
-                            tmem_ld8(ta + kAccIm, *reinterpret_cast<float(*)[8]>(vi));
-                            tmem_ld4(ta + kAccIm + 8, *reinterpret_cast<uint32_t(*)[4]>(vi + 8));
+                            tmem_ld8(ta + kTcAccIm, *reinterpret_cast<float(*)[8]>(vi));
+                            tmem_ld4(ta + kTcAccIm + 8, *reinterpret_cast<uint32_t(*)[4]>(vi + 8));
                         }
                         if (q > 0) {
                             // MMAs of tile q - 1 done: its result can be drained, the A tile reused
@@ -1547,7 +1578,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         float pv[8];
                         if (q > 0) {
                             // ---- result of tile q - 1: rows (r', e, k) x (s, re/im) ----
-                            tmem_ld8(tmem + ((uint32_t)(dq * 32) << 16) + (((tq - 1) & 1) ? kPostCol1 : kPostCol0) +
+                            tmem_ld8(tmem + ((uint32_t)(dq * 32) << 16) + (((tq - 1) & 1) ? kTcPost1 : kTcPost0) +
                                          (uint32_t)(8 * dsub), pv);
                             tmem_ld_wait();
                         }
@@ -1620,7 +1651,7 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
     const uint32_t bx = bsz + 72 * kXs * 4, nv = 2 * kPostAPlane;
     prm.off_b = take(bx > nv ? bx : nv, 1024);
     prm.off_x = prm.off_b + bsz;
-    prm.off_g = take(kTcRing * GG::XP_SLICE, 1024);
+    prm.off_g = take(kTcRing * kTcPairBytes, 1024);
     prm.off_a = take(2 * 8192, 1024);
     const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
     prm.off_df = take(2u * 2u * GG::DA_GROUPS * 2u * rows * 16u, 1024);
