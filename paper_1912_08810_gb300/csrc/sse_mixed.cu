@@ -38,7 +38,6 @@ constexpr int kRowsMax = 128;    // MMA M
 constexpr int kCh = 144;         // MMA N: channels of a 12 x 12 block
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccIm = 256; // TMEM column of the imaginary accumulator
-constexpr uint32_t kPreCol0 = 192, kPreCol1 = 448;  // pre-product accumulators (64 columns each)
 constexpr uint64_t kWaitNs = 250000000ull;  // bound on every device-side wait (0.25 s)
 constexpr int kMaxSlots = 32;
 constexpr int kVStride = 73;     // row stride (floats) of the drained accumulator tile
@@ -64,13 +63,12 @@ struct Geo {
     static constexpr int DA_SBO_B = (DA_K / 8) * 128;  // 256 bytes
     static constexpr int DA_B_PLANE = (kCh / 8) * DA_SBO_B;
     static constexpr int DA_GROUPS = 16;               // 8-row groups of the 128-row tile
-    // Tensor-core pre-product X = dH . G (with a re-encoded G): rows (i, r, re/im) = 72,
-    // columns (k', t) = 12 Nkz padded to 64, K = (re/im of G, u) = 24 padded to 32.
-    static constexpr int XP_N = 64;
-    static constexpr int XP_SLICE = 8192;              // one (E', f) slice: hi plane + lo plane
-    static constexpr int XP_XS = 61;                   // row stride (floats) of the X transpose buffer
 };
 
+
+// Re-encoded G for the tensor-core pre-product X = dH . G: one (E', f) slice holds rows
+// (k', t) = 12 Nkz padded to 64 by K = (re/im of G, u) = 24 padded to 32, hi then lo plane.
+constexpr int kXpSlice = 8192;
 
 constexpr int kMaxInst = 64;  // instances per launch (the descriptors travel as kernel parameters)
 
@@ -194,10 +192,9 @@ __device__ __forceinline__ double2 final_of<double2>(float2 v) { return make_dou
 template <>
 __device__ __forceinline__ float2 final_of<float2>(float2 v) { return v; }
 
-template <int NK, typename CT, bool V3>
+template <int NK, typename CT>
 __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_constant__ MixParams prm) {
     using GG = Geo<NK>;
-    static_assert(!V3 || GG::DA, "the tensor-core pre-product runs with the direct Toeplitz form");
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nw = prm.nw;
@@ -215,30 +212,25 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     uint8_t *sTab = smem + prm.off_df;                // Toeplitz row table of the current slot
     float2 *sDh = (float2 *)(smem + prm.off_dh);      // [3][144] fp32 dH of the current slot
     // Jobs (tile, slot) of a unit run slot-major, so the per-slot tables are built once per
-    // slot and reused by the unit's tiles; the direct form without the pre-product keeps
-    // tile-major order because its drained accumulators overlay the direct table.
-    constexpr bool SLOT_OUTER = V3 || !GG::DA;
+    // slot and reused by the unit's tiles; the direct form keeps tile-major order because its
+    // drained accumulators overlay the direct table.
+    constexpr bool SLOT_OUTER = !GG::DA;
     // epilogue: the accumulators are drained in EP_PARTS column blocks of EP_R rows r
-    constexpr int EP_PARTS = V3 ? 3 : 2;
+    constexpr int EP_PARTS = 2;
     constexpr int EP_COLS = kCh / EP_PARTS, EP_STRIDE = EP_COLS + 1, EP_R = EP_COLS / 12;
     constexpr int EP_RB = EP_R / 2, EP_NSB = 6 / EP_RB, EP_S = 12 / EP_NSB;
     static_assert(EP_STRIDE * 2 * kRowsMax * 4 <= 2 * kRowsMax * kVStride * 4, "drain buffer");
-    // drained accumulators: overlay B and A; the direct form: the per-slot table, or with the
-    // pre-product the B stages and the X buffer
-    float *sV = (float *)(V3 ? smem + prm.off_b : GG::DA ? smem + prm.off_df : smem + prm.off_b);
+    // drained accumulators: overlay B and A, or (direct form) the per-slot table
+    float *sV = (float *)(GG::DA ? smem + prm.off_df : smem + prm.off_b);
     static_assert(!GG::DA || GG::TE == GG::DA_TE, "direct form expects 8 energies per tile");
     uint64_t *bar_mma = (uint64_t *)(smem + prm.off_bar);
     uint64_t *bar_g = bar_mma + 2;                   // [3] (two used without the pre-product)
     uint64_t *bar_job = bar_mma + 5;
     uint64_t *bar_fin = bar_mma + 6;                 // only for draining MMAs on abort
-    uint64_t *bar_pre = bar_mma + 7;                 // [2] pre-product MMAs done
     uint32_t *s_tmem = (uint32_t *)(bar_mma + 9);
     int *s_abort = (int *)(s_tmem + 1);
     int *s_nvalid = s_abort + 1;
     long long *s_unit = (long long *)(smem + prm.off_bar + 128);
-    uint8_t *sPreB = smem + prm.off_g;                // pre-product: [3] G slices (TMA)
-    uint8_t *sApre = smem + prm.off_a;                // pre-product: dH operand [hi, lo]
-    float *sX = (float *)(smem + prm.off_x);          // pre-product: X rows (i, r, re/im) x (k', t)
     int *s_slot = (int *)(s_unit + 1);                // [kMaxSlots] valid slot indices
     int *s_f = s_slot + kMaxSlots;                    // [kMaxSlots] their neighbour atoms
 
@@ -250,8 +242,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         mbar_init(&bar_g[2], 1);
         mbar_init(bar_job, 1);
         mbar_init(bar_fin, 1);
-        mbar_init(&bar_pre[0], 1);
-        mbar_init(&bar_pre[1], 1);
         fence_mbar_init();
         *s_abort = 0;
     }
@@ -265,7 +255,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
     const uint32_t tmem = *s_tmem;
 
     // Per-thread A-builder row: thread -> (accumulator q, row m).
-    int last_g[3] = {-1, -1, -1};  // thread 0: last stage whose G slice went to each buffer
     const int aq = tid >> 7, am = tid & 127;
     const bool arow_ok = am < GG::ROWS;
     const int ae = am / (3 * NK), ak = (am / 3) % NK, aj = am % 3;
@@ -379,46 +368,9 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         }
     };
 
-    // Thread 0: bulk-copy the re-encoded G slice of stage g (one 8 KB copy; the zero slice
-    // stands in for energies below or above the grid) into pre-product buffer gg % 3.
-    auto issue_pre = [&](int g, const Pos &q) {
-        const int t = q.t, vs = q.vs, st = q.st;
-        const int f = s_f[vs];
-        const int Ep = t * GG::TE - omega_max + st;
-        const long long slice = (Ep >= 0 && Ep < d.ne) ? (long long)Ep * d.na + f : (long long)d.ne * d.na;
-        const int gg = g_base + g;
-        uint64_t *bar = &bar_g[gg % 3];
-        mbar_arrive_expect_tx(bar, GG::XP_SLICE);
-        bulk_g2s(sPreB + (gg % 3) * GG::XP_SLICE, I.gws[sign] + slice * GG::XP_SLICE, GG::XP_SLICE, bar);
-        last_g[gg % 3] = gg;
-    };
-    // Thread 0: pre-product MMAs of stage g into D_pre[gg & 1] once its G slice is in.
-    auto issue_premma = [&](int g) -> bool {
-        const int gg = g_base + g;
-        if (!mbar_wait_bounded(&bar_g[gg % 3], (gg / 3) & 1, kWaitNs)) return false;
-        tc_fence_after();
-        constexpr uint32_t idesc_x = idesc_bf16_f32(kRowsMax, GG::XP_N);
-        const uint32_t a0 = smem_u32(sApre), b0 = smem_u32(sPreB + (gg % 3) * GG::XP_SLICE);
-        const uint32_t dx = tmem + ((gg & 1) ? kPreCol1 : kPreCol0);
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t ah = smem_desc(a0 + ks * 256, 128, 512), al = smem_desc(a0 + 8192 + ks * 256, 128, 512);
-            const uint64_t bh = smem_desc(b0 + ks * 256, 128, 512), bl = smem_desc(b0 + 4096 + ks * 256, 128, 512);
-            mma_ss(dx, ah, bh, idesc_x, ks ? 1u : 0u);
-            mma_ss(dx, ah, bl, idesc_x, 1u);
-            mma_ss(dx, al, bh, idesc_x, 1u);
-        }
-        mma_commit(&bar_pre[gg & 1]);
-        return true;
-    };
     Pos cur{t_begin, 0, 0};  // the stage being built
     Pos pf{t_begin, 0, 0};   // thread 0: the next stage to prefetch
-    if constexpr (V3) {
-        if (tid == 0 && total > 0) issue_pre(0, pf), advance(pf);
-        if (tid == 0 && total > 1) issue_pre(1, pf), advance(pf);
-    } else {
-        if (tid == 0 && total > 0) issue_g(0, pf), advance(pf);
-    }
+    if (tid == 0 && total > 0) issue_g(0, pf), advance(pf);
 
     for (int g = 0; g < total && !abort; ++g, advance(cur)) {
         const int t = cur.t, vs = cur.vs, st = cur.st;
@@ -426,9 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         const int sb = gg & 1;
         const int E0 = t * GG::TE;
         const bool job_first = st == 0, job_last = st == prm.nst - 1;
-        // first stage of a slot's first job / last stage of a slot's last job
+        // first stage of a slot's first job
         const bool slot_first = job_first && (!SLOT_OUTER || t == t_begin);
-        const bool slot_last = job_last && (!SLOT_OUTER || t + 1 == t_end);
 
         // another CTA timed out: stop early instead of waiting out every bound
         if (job_first && tid == 0 && *(volatile int32_t *)prm.status != 0) *s_abort = 1;
@@ -483,43 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                     *(uint4 *)(sTab + base_hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                     *(uint4 *)(sTab + base_lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                 }
-                if constexpr (V3) {
-                    // pre-product operand A_pre[(i, r, re/im), (pc, u)]: the complex product
-                    // dH_i . G as a real one (rows pr = re: (Re dH, -Im dH); pr = im: (Im dH, Re dH))
-                    for (int x = tid; x < kRowsMax * 4; x += kThreads) {
-                        const int m = x >> 2, kg = x & 3;
-                        float v[8];
-#pragma unroll
-                        for (int xx = 0; xx < 8; ++xx) {
-                            const int kk = kg * 8 + xx;
-                            float val = 0.f;
-                            if (m < 72 && kk < 24) {
-                                const int pr = m & 1, r = (m >> 1) % 12, i = (m >> 1) / 12, pc = kk / 12, u = kk % 12;
-                                const float2 h = sDh[i * kCh + r * 12 + u];
-                                val = pr ? (pc ? h.x : h.y) : (pc ? -h.y : h.x);
-                            }
-                            v[xx] = val;
-                        }
-                        uint32_t hv[4], lv[4];
-#pragma unroll
-                        for (int xx = 0; xx < 4; ++xx) {
-                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
-                            hv[xx] = hl.x;
-                            lv[xx] = hl.y;
-                        }
-                        uint8_t *dst = sApre + (m >> 3) * 512 + kg * 128 + (m & 7) * 16;
-                        *(uint4 *)dst = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *(uint4 *)(dst + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-                    }
-                    fence_proxy_async_smem();
-                }
                 __syncthreads();
-                if constexpr (V3) {
-                    if (tid == 0 && !issue_premma(g)) {
-                        *s_abort = 1;
-                        atomicExch(prm.status, 1);
-                    }
-                }
             } else {
             // Row table of the real-part accumulator's Toeplitz operand: one row per
             // (k, j, w0), w0 in [0, nw0); entry (p, i, k', re/im) = (Re T, -Im T) with
@@ -561,15 +476,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 
         uint8_t *gbuf = sG + sb * prm.g_stage;
         float2 *g32 = (float2 *)gbuf;  // [p][k'][u][t] complex fp32
-        if constexpr (V3) {
-            if (tid == 0 && g + 2 < total) issue_pre(g + 2, pf), advance(pf);
-            // X of this stage: its pre-product MMAs were issued one stage earlier
-            if (!mbar_wait_bounded(&bar_pre[gg & 1], (gg >> 1) & 1, kWaitNs)) {
-                *s_abort = 1;
-                atomicExch(prm.status, 1);
-            }
-            tc_fence_after();
-        } else {
         if (tid == 0 && g + 1 < total) issue_g(g + 1, pf), advance(pf);
 
         // ---- G blocks of this stage: wait, convert to fp32 in place, zero the gaps ----
@@ -605,7 +511,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                 if (x < NE_) g32[x] = v[r];
             }
         }
-        }  // !V3
 
         // ---- the stage buffers must be free: MMAs of stage g - 2 complete ----
         if (gg >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((gg >> 1) - 1) & 1, kWaitNs)) {
@@ -618,55 +523,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         uint8_t *abase = sA + sb * (4 * GG::A_PLANE);
         uint8_t *bda = sB + sb * (4 * GG::DA_B_PLANE);  // direct form: [re, im][hi, lo] planes
 
-        if constexpr (V3) {
-            // ---- X from the pre-product accumulator: TMEM rows (i, r, re/im) -> sX ----
-            if (warp < 3) {
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + ((gg & 1) ? kPreCol1 : kPreCol0);
-                const int m = warp * 32 + lane;
-                uint32_t x0[32], x1[32];
-                tmem_ld32(taddr, x0);
-                tmem_ld32(taddr + 32, x1);
-                tmem_ld_wait();
-                if (m < 72) {
-                    float *row = sX + m * GG::XP_XS;
-#pragma unroll
-                    for (int x = 0; x < 32; ++x) row[x] = __uint_as_float(x0[x]);
-#pragma unroll
-                    for (int x = 0; x < NK * 12 - 32; ++x) row[32 + x] = __uint_as_float(x1[x]);
-                }
-                tc_fence_before();
-            }
-            __syncthreads();
-            // ---- X -> B planes [re, im][hi, lo] of channel n = (r, t), K index i * Nkz + k' ----
-            for (int item = tid; item < 2 * kCh; item += kThreads) {
-                const int n = item % kCh, pr = item / kCh, r = n / 12, tt = n % 12;
-                float xv[16];
-#pragma unroll
-                for (int kk = 0; kk < 16; ++kk) {
-                    xv[kk] = 0.f;
-                    if (kk < 3 * NK) {
-                        const int i = kk / NK, kp = kk % NK;
-                        xv[kk] = sX[((i * 12 + r) * 2 + pr) * GG::XP_XS + kp * 12 + tt];
-                    }
-                }
-                uint32_t hv[8], lv[8];
-#pragma unroll
-                for (int x = 0; x < 8; ++x) {
-                    const uint2 hl = split2_bf16(xv[2 * x], xv[2 * x + 1]);
-                    hv[x] = hl.x;
-                    lv[x] = hl.y;
-                }
-                const uint32_t row_off = (n >> 3) * GG::DA_SBO_B + (n & 7) * 16;
-                uint8_t *ph = bda + (2 * pr) * GG::DA_B_PLANE, *pl = ph + GG::DA_B_PLANE;
-#pragma unroll
-                for (int gq = 0; gq < 2; ++gq) {
-                    *(uint4 *)(ph + row_off + gq * 128) = make_uint4(hv[4 * gq], hv[4 * gq + 1], hv[4 * gq + 2], hv[4 * gq + 3]);
-                    *(uint4 *)(pl + row_off + gq * 128) = make_uint4(lv[4 * gq], lv[4 * gq + 1], lv[4 * gq + 2], lv[4 * gq + 3]);
-                }
-            }
-        }
         // ---- X slices: X_i[k'][r, t] = sum_u dH_i[r, u] G[k'][u, t] -> B (bf16 hi / lo) ----
-        for (int item = tid; item < (V3 ? 0 : GG::P * kCh); item += kThreads) {
+        for (int item = tid; item < GG::P * kCh; item += kThreads) {
             const int p = item / kCh, n = item % kCh, r = n / 12, tt = n % 12;
             uint32_t hw[GG::KS / 2], lw[GG::KS / 2];
 #pragma unroll
@@ -767,13 +625,6 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         // ---- MMAs of this stage (one thread) ----
         if (tid == 0) {
             tc_fence_after();
-            if constexpr (V3) {
-                // the next stage's pre-product first, so its X is ready while these MMAs run
-                if (!slot_last && g + 1 < total && !issue_premma(g + 1)) {
-                    *s_abort = 1;
-                    atomicExch(prm.status, 1);
-                }
-            }
             if constexpr (GG::DA) {
                 // A: windows of the direct table starting at row (nw - 1 - st) + (TE - 1)
                 constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
@@ -926,15 +777,9 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         if (tid == 0) mma_commit(bar_fin);  // arrives once every MMA issued so far is done
         mbar_wait_bounded(bar_fin, 0, kWaitNs);
         // the bulk copies of the aborted stage and of the one prefetched after it
-        if constexpr (V3) {
-            if (tid == 0)
-                for (int b = 0; b < 3; ++b)
-                    if (last_g[b] >= 0) mbar_wait_bounded(&bar_g[b], (last_g[b] / 3) & 1, kWaitNs);
-        } else {
-            if (abort_g >= 0) mbar_wait_bounded(&bar_g[abort_g & 1], (abort_g >> 1) & 1, kWaitNs);
-            if (abort_g + 1 < abort_total)
-                mbar_wait_bounded(&bar_g[(abort_g + 1) & 1], ((abort_g + 1) >> 1) & 1, kWaitNs);
-        }
+        if (abort_g >= 0) mbar_wait_bounded(&bar_g[abort_g & 1], (abort_g >> 1) & 1, kWaitNs);
+        if (abort_g + 1 < abort_total)
+            mbar_wait_bounded(&bar_g[(abort_g + 1) & 1], ((abort_g + 1) >> 1) & 1, kWaitNs);
     }
     tc_fence_before();
     __syncthreads();
@@ -1403,7 +1248,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                                 const int Ep = t * GG::TE - omega_max + st;
                                 if (Ep >= 0 && Ep < d.ne) slice = (long long)Ep * d.na + f;
                             }
-                            const uint8_t *sl = gws + slice * GG::XP_SLICE;
+                            const uint8_t *sl = gws + slice * kXpSlice;
                             bulk_g2s(dst + h * 4096, sl, 4096, &bar_g[slot]);
                             bulk_g2s(dst + 8192 + h * 4096, sl + 4096, 4096, &bar_g[slot]);
                         }
@@ -1663,7 +1508,7 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
 }
 
 template <int NK>
-uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm, bool v3) {
+uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
     using GG = Geo<NK>;
     uint32_t off = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
@@ -1676,21 +1521,12 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm, bool v3)
     const uint32_t dtmp = (uint32_t)(NK * d.nw * 9 * 8);
     prm.g_stage = (uint32_t)(GG::P * NK * kCh * cbytes);
     if (GG::DA) {
-        // B stages, raw G (or the pre-product's G slices and dH operand and X buffer), the
-        // direct table (the drained accumulators overlay it)
+        // B stages, raw G, the direct table (the drained accumulators overlay it)
         const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
-        if (v3) {
-            const uint32_t bx = bsz + 72 * GG::XP_XS * 4, nv3 = 2 * kRowsMax * (kCh / 3 + 1) * 4;
-            prm.off_b = take(bx > nv3 ? bx : nv3, 1024);
-            prm.off_x = prm.off_b + bsz;
-            prm.off_g = take(3 * GG::XP_SLICE, 1024);
-            prm.off_a = take(2 * 8192, 1024);
-        } else {
-            prm.off_b = take(bsz, 1024);
-            prm.off_a = prm.off_b;
-            prm.off_g = take(2 * prm.g_stage, 128);
-            prm.off_x = 0;
-        }
+        prm.off_b = take(bsz, 1024);
+        prm.off_a = prm.off_b;
+        prm.off_g = take(2 * prm.g_stage, 128);
+        prm.off_x = 0;
         const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
         const uint32_t tab = 2u * 2u * GG::DA_GROUPS * 2u * rows * 16u;
         prm.off_df = take(tab > need_v ? tab : need_v, 1024);
@@ -1753,7 +1589,7 @@ long long inst_units(const InstDesc &I) { return (long long)I.nsign * I.na * I.n
 template <int NK, typename CT, bool V3>
 sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *status) {
     using GG = Geo<NK>;
-    smem = V3 ? tc_smem_bytes(d, prm) : mixed_smem_bytes<NK>(d, sizeof(CT), prm, false);
+    smem = V3 ? tc_smem_bytes(d, prm) : mixed_smem_bytes<NK>(d, sizeof(CT), prm);
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
         return SSE_E_INVALID_ARG;
@@ -1767,7 +1603,7 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
     if constexpr (V3)
         e = cudaFuncSetAttribute(sse_tc_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else
-        e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mixed kernel)");
     return SSE_OK;
@@ -1834,7 +1670,7 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     if constexpr (V3)
         sse_tc_kernel<CT><<<(unsigned)prm.total_units, kTcThreads, smem, st>>>(prm);
     else
-        sse_mixed_kernel<NK, CT, false><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
+        sse_mixed_kernel<NK, CT><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
     timing_mark(p, ts, 2, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch sse_mixed_kernel");
@@ -1878,7 +1714,7 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
         if constexpr (V3)
             sse_tc_kernel<CT><<<(unsigned)grid, kTcThreads, smem, st>>>(prm);
         else
-            sse_mixed_kernel<NK, CT, false><<<(unsigned)grid, kThreads, smem, st>>>(prm);
+            sse_mixed_kernel<NK, CT><<<(unsigned)grid, kThreads, smem, st>>>(prm);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "launch persistent sse_mixed_kernel");
     }
@@ -1944,11 +1780,11 @@ sse_status mixed_plan_init(Plan &p) {
     uint32_t smem = 0;
     const size_t cb = elem_bytes(p.geo.dtype);
     switch (d.nkz) {
-        case 1: smem = mixed_smem_bytes<1>(d, cb, prm, false); p.tile_e = tile_e_of<1>(); break;
-        case 2: smem = mixed_smem_bytes<2>(d, cb, prm, false); p.tile_e = tile_e_of<2>(); break;
-        case 3: smem = mixed_smem_bytes<3>(d, cb, prm, false); p.tile_e = tile_e_of<3>(); break;
-        case 4: smem = mixed_smem_bytes<4>(d, cb, prm, false); p.tile_e = tile_e_of<4>(); break;
-        default: smem = mixed_smem_bytes<5>(d, cb, prm, false); p.tile_e = tile_e_of<5>(); break;
+        case 1: smem = mixed_smem_bytes<1>(d, cb, prm); p.tile_e = tile_e_of<1>(); break;
+        case 2: smem = mixed_smem_bytes<2>(d, cb, prm); p.tile_e = tile_e_of<2>(); break;
+        case 3: smem = mixed_smem_bytes<3>(d, cb, prm); p.tile_e = tile_e_of<3>(); break;
+        case 4: smem = mixed_smem_bytes<4>(d, cb, prm); p.tile_e = tile_e_of<4>(); break;
+        default: smem = mixed_smem_bytes<5>(d, cb, prm); p.tile_e = tile_e_of<5>(); break;
     }
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
