@@ -978,15 +978,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bar_pre = bars + kTcRing;          // pre-product of a pair done
     uint64_t *bar_bready = bars + kTcRing + 1;   // [2] B of a stage built
     uint64_t *bar_job = bars + kTcRing + 3;      // last MMAs of a job done
-    uint64_t *bar_slot = bars + kTcRing + 4;     // slot tables copied in
+    uint64_t *bar_slot = bars + kTcRing + 4;     // the slot's pre- and post-product operands copied in
     uint64_t *bar_fin = bars + kTcRing + 5;      // abort: every MMA issued so far done
     uint64_t *bar_mma = bars + kTcRing + 6;      // [2] main MMAs of a stage done (B buffer free)
     uint64_t *bar_apost = bars + kTcRing + 8;    // post-product A tile built
     uint64_t *bar_post = bars + kTcRing + 9;     // [2] post-product MMAs of a tile done
     uint64_t *bar_empty = bars + kTcRing + 11;   // [kTcRing] pre-product done with a ring slot
     uint64_t *bar_slotfree = bars + 2 * kTcRing + 11;  // every MMA of the previous slot done
-    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 12);
-    static_assert((2 * kTcRing + 12) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
+    uint64_t *bar_tab = bars + 2 * kTcRing + 12;       // the slot's direct table copied in
+    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 13);
+    static_assert((2 * kTcRing + 13) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
     // abort flags: builders write slot g & 1 during stage g and all read it after the stage's
     // last barrier (the next write to that slot comes after another barrier); the control
     // warp has its own flag
@@ -1005,6 +1006,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(&bar_bready[1], kTcBuilders);
         mbar_init(bar_job, 1);
         mbar_init(bar_slot, 1);
+        mbar_init(bar_tab, 1);
         mbar_init(bar_slotfree, 1);
         mbar_init(bar_fin, 1);
         mbar_init(&bar_mma[0], 1);
@@ -1153,13 +1155,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const bool job_first = m.st == 0, job_last = m.st == prm.nst - 1;
                     const int slot_rem = slot_len - 1 - o;  // stages after this one in its slot
                     if (o == 0) {
-                        ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs);
-                        ++slot_ctr;
-                        if (!ok) break;
+                        if (!(ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs))) break;
                         tc_fence_after();
                         if (!(ok = premma())) break;
                     }
                     if (!(ok = mbar_wait_bounded(&bar_bready[gg & 1], (gg >> 1) & 1, kWaitNs))) break;
+                    if (o == 0) {
+                        ok = mbar_wait_bounded(bar_tab, slot_ctr & 1, kWaitNs);
+                        ++slot_ctr;
+                        if (!ok) break;
+                    }
                     tc_fence_after();
                     // X of the next pair ahead of this stage's main MMAs: the builders drained the
                     // TMEM buffer at this (first) stage of the current pair
@@ -1221,39 +1226,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 const int slot_len = (t_end - t_begin) * prm.nst;
                 const long long zero = (long long)d.ne * d.na;  // the zero slice
                 bool ok = true;
+                // one pair of slices (stage offsets o, o + 1 of the slot) into the next ring slot
+                auto issue_pair = [&](int o, int f) -> bool {
+                    const int slot = pair_ctr % kTcRing, use = pair_ctr / kTcRing;
+                    // ring slot free: the pre-product of its previous pair is done (first use: free)
+                    if (!mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs)) return false;
+                    mbar_arrive_expect_tx(&bar_g[slot], kTcPairBytes);
+                    uint8_t *dst = sRing + slot * kTcPairBytes;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        // the zero slice stands in for energies below or above the grid and for
+                        // the missing second stage of an odd-length slot
+                        long long slice = zero;
+                        if (o + h < slot_len) {
+                            const int t = t_begin + (o + h) / prm.nst, st = (o + h) % prm.nst;
+                            const int Ep = t * GG::TE - omega_max + st;
+                            if (Ep >= 0 && Ep < d.ne) slice = (long long)Ep * d.na + f;
+                        }
+                        const uint8_t *sl = gws + slice * kXpSlice;
+                        bulk_g2s(dst + h * 4096, sl, 4096, &bar_g[slot]);
+                        bulk_g2s(dst + 8192 + h * 4096, sl + 4096, 4096, &bar_g[slot]);
+                    }
+                    last_g[slot] = pair_ctr++;
+                    return true;
+                };
+                const int npairs = (slot_len + 1) / 2;
                 for (int vs = 0; vs < nvalid && ok; ++vs) {
-                    // a new slot: its tables replace the previous slot's once every MMA that read
-                    // those is done (the CTA's first slot: nothing to wait for)
+                    const int f = s_f[vs];
+                    // the slot's first pairs go ahead of its tables: they only need free ring slots
+                    int pr = 0;
+                    for (; pr < npairs && pr < kTcRing && ok; ++pr) ok = issue_pair(2 * pr, f);
+                    if (!ok) break;
+                    // its tables replace the previous slot's once every MMA that read those is
+                    // done (the CTA's first slot: nothing to wait for)
                     if (!(ok = mbar_wait_bounded(bar_slotfree, (slot_cp & 1) ^ 1, kWaitNs))) break;
+                    // the small operands first: the pre-product can start while the table streams in
                     const uint8_t *src = I.sws[sign] + ((size_t)a * d.nb + s_slot[vs]) * ebytes;
-                    mbar_arrive_expect_tx(bar_slot, ebytes);
-                    bulk_g2s(sTab, src, tbytes, bar_slot);
+                    mbar_arrive_expect_tx(bar_slot, 16384 + 2 * kPostBPlane);
                     bulk_g2s(sApre, src + tbytes, 16384, bar_slot);
                     bulk_g2s(sBpost, src + tbytes + 16384, 2 * kPostBPlane, bar_slot);
+                    mbar_arrive_expect_tx(bar_tab, tbytes);
+                    bulk_g2s(sTab, src, tbytes, bar_tab);
                     ++slot_cp;
-                    const int f = s_f[vs];
-                    for (int o = 0; o < slot_len; o += 2, ++pair_ctr) {
-                        const int slot = pair_ctr % kTcRing, use = pair_ctr / kTcRing;
-                        // ring slot free: the pre-product of its previous pair is done (first use: free)
-                        if (!(ok = mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
-                        mbar_arrive_expect_tx(&bar_g[slot], kTcPairBytes);
-                        uint8_t *dst = sRing + slot * kTcPairBytes;
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            // the zero slice stands in for energies below or above the grid and for
-                            // the missing second stage of an odd-length slot
-                            long long slice = zero;
-                            if (o + h < slot_len) {
-                                const int t = t_begin + (o + h) / prm.nst, st = (o + h) % prm.nst;
-                                const int Ep = t * GG::TE - omega_max + st;
-                                if (Ep >= 0 && Ep < d.ne) slice = (long long)Ep * d.na + f;
-                            }
-                            const uint8_t *sl = gws + slice * kXpSlice;
-                            bulk_g2s(dst + h * 4096, sl, 4096, &bar_g[slot]);
-                            bulk_g2s(dst + 8192 + h * 4096, sl + 4096, 4096, &bar_g[slot]);
-                        }
-                        last_g[slot] = pair_ctr;
-                    }
+                    for (; pr < npairs && ok; ++pr) ok = issue_pair(2 * pr, f);
                 }
                 if (!ok) {
                     *s_abort_prd = 1;
@@ -1376,8 +1391,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     float2 old[4];
                     CT *dst = S;
                     // Tile q: its A is built once the MMAs of tile q - 1 are done (one A buffer);
-                    // the accumulator columns it needs are loaded before that wait, and the FP64
-                    // update of Sigma with tile q - 1 runs after tile q is handed to the MMAs.
+                    // the accumulator columns it needs are loaded before that wait, and tile
+                    // q - 1's result is drained and added to Sigma after tile q is handed to the MMAs.
                     for (int q = 0; q <= 4; ++q) {
                         const int tq = tile_ctr + q;  // CTA-wide index of tile q
                         uint32_t vr[12], vi[12];
@@ -1420,24 +1435,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                                 *(uint4 *)(rbase + 9 * 128 + kPostAPlane) = make_uint4(0u, 0u, 0u, 0u);
                             }
                         }
-                        float pv[8];
-                        if (q > 0) {
-                            // ---- result of tile q - 1: rows (r', e, k) x (s, re/im) ----
-                            tmem_ld8(tmem + ((uint32_t)(dq * 32) << 16) + (((tq - 1) & 1) ? kTcPost1 : kTcPost0) +
-                                         (uint32_t)(8 * dsub), pv);
-                            tmem_ld_wait();
-                        }
                         tc_fence_before();
                         if (q < 4) {
                             fence_proxy_async_smem();
                             mbar_arrive(bar_apost);
                         }
+                        float pv[8];
+                        if (q > 0) {
+                            // ---- result of tile q - 1: rows (r', e, k) x (s, re/im); its TMEM
+                            // columns are next written by tile q + 1, handed over after this ----
+                            tmem_ld8(tmem + ((uint32_t)(dq * 32) << 16) + (((tq - 1) & 1) ? kTcPost1 : kTcPost0) +
+                                         (uint32_t)(8 * dsub), pv);
+                            tmem_ld_wait();
+                            tc_fence_before();
+                        }
                         if (q > 0 && dlive) {
+                            // first slot: store; middle slots: add in place without waiting; last
+                            // slot: the sum so far (read one tile ahead) plus this one, in the output type
 #pragma unroll
                             for (int s2 = 0; s2 < 4; ++s2) {
-                                const float2 v = make_float2(pv[2 * s2] + old[s2].x, pv[2 * s2 + 1] + old[s2].y);
-                                if (last_slot) dst[s2] = final_of<CT>(v);
-                                else *partial_of(dst + s2) = v;
+                                const float2 v = make_float2(pv[2 * s2], pv[2 * s2 + 1]);
+                                if (first_slot && last_slot) dst[s2] = final_of<CT>(v);
+                                else if (first_slot) *partial_of(dst + s2) = v;
+                                else if (!last_slot || sizeof(CT) == 8) red_add_f2(partial_of(dst + s2), v);
+                                else dst[s2] = final_of<CT>(make_float2(v.x + old[s2].x, v.y + old[s2].y));
                             }
                         }
                         if (q < 4) {
@@ -1447,7 +1468,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 #pragma unroll
                             for (int s2 = 0; s2 < 4; ++s2) {
                                 old[s2] = make_float2(0.f, 0.f);
-                                if (dlive && !first_slot) old[s2] = *partial_of(dst + s2);
+                                if (dlive && !first_slot && last_slot && sizeof(CT) == 16) old[s2] = *partial_of(dst + s2);
                             }
                         }
                     }
@@ -1473,7 +1494,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (abort && prd && lane == 0) {
         for (int b = 0; b < kTcRing; ++b)
             if (last_g[b] >= 0) mbar_wait_bounded(&bar_g[b], (last_g[b] / kTcRing) & 1, kWaitNs);
-        if (slot_cp > 0) mbar_wait_bounded(bar_slot, (slot_cp - 1) & 1, kWaitNs);
+        if (slot_cp > 0) {
+            mbar_wait_bounded(bar_slot, (slot_cp - 1) & 1, kWaitNs);
+            mbar_wait_bounded(bar_tab, (slot_cp - 1) & 1, kWaitNs);
+        }
     }
     tc_fence_before();
     __syncthreads();

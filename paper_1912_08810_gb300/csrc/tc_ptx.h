@@ -74,6 +74,11 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Fire-and-forget atomic add of two floats to global memory (relaxed, no return value).
+__device__ __forceinline__ void red_add_f2(float2 *p, float2 v) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // ---- bulk copies (TMA, non-tensor form) ------------------------------------------------
 
 // 1-D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global
