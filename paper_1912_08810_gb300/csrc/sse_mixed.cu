@@ -127,14 +127,20 @@ __device__ __forceinline__ uint4 to_im_pairs(uint4 v) {
 }
 
 // G of one sign re-encoded for the tensor-core pre-product: slice (E', f) holds, for rows
-// n' = k' * 12 + t (12 Nkz used, 64 rows) and K = pc * 12 + u (24 used, 32), the bf16 hi
-// plane then the lo plane of the pc-part of G[k', E', f][u, t], in the K-major core-matrix
-// layout (SBO 512, LBO 128).  One CTA per slice.
+// n' = (t / 4) * 4 Nkz + k' * 4 + t % 4 (12 Nkz used, 64 rows) and K = pc * 12 + u (24 used,
+// 32), the bf16 hi plane then the lo plane of the pc-part of G[k', E', f][u, t], in the
+// K-major core-matrix layout (SBO 512, LBO 128).  One CTA per slice.  The row order makes a
+// 16-lane TMEM load of the product hand each builder thread whole K rows of the main MMA's B.
 template <typename CT>
 __global__ void __launch_bounds__(256) sse_split_g_kernel(const CT *__restrict__ G, uint8_t *__restrict__ ws,
                                                           int ne, int na, int nkz) {
+    __shared__ float2 sg[5 * kCh];  // G[k', E', f] of the slice (Nkz = 5), read contiguously
+    if (nkz > 5) return;           // the tensor-core form serves Nkz = 5 only
     const long long slice = blockIdx.x;
     const int E = (int)(slice / na), f = (int)(slice % na);
+    for (int x = threadIdx.x; x < nkz * kCh; x += 256)
+        sg[x] = load_c32(G + (((size_t)(x / kCh) * ne + E) * na + f) * kCh + x % kCh);
+    __syncthreads();
     const int np = threadIdx.x >> 2, kg = threadIdx.x & 3;
     float v[8];
 #pragma unroll
@@ -142,8 +148,9 @@ __global__ void __launch_bounds__(256) sse_split_g_kernel(const CT *__restrict__
         const int kk = kg * 8 + xx;
         float val = 0.f;
         if (np < nkz * 12 && kk < 24) {
-            const int kp = np / 12, t = np % 12, pc = kk / 12, u = kk % 12;
-            const float2 c = load_c32(G + (((size_t)kp * ne + E) * na + f) * kCh + u * 12 + t);
+            const int blk = np / (4 * nkz), kp = (np % (4 * nkz)) / 4, t = 4 * blk + np % 4;
+            const int pc = kk / 12, u = kk % 12;
+            const float2 c = sg[kp * kCh + u * 12 + t];
             val = pc ? c.y : c.x;
         }
         v[xx] = val;
@@ -810,7 +817,6 @@ constexpr uint32_t kTcAccIm = 160;             // Im V (Re V at 0), 144 columns 
 constexpr uint32_t kTcPost0 = 320, kTcPost1 = 352;  // post-product accumulators, 32 columns each
 constexpr uint32_t kTcPre = 384;               // X of a pair of stages, 2 x 64 columns
 constexpr int kDhJ = 160;    // float2 per direction j of the padded dH copy
-constexpr int kXs = 76;      // row stride (floats) of the X buffer
 // Post-product Sigma_slot[(e, k), r, s] = sum_{j, t} V_j[(e, k)][r, t] conj(dH_j[s, t]) on the
 // tensor cores: rows (r', e, k) of an M tile (three rows r per tile, four tiles), K = (j, t,
 // re/im of V) = 72 padded to 80, N = (s, re/im of the product) = 24 padded to 32.
@@ -819,14 +825,6 @@ constexpr uint32_t kPostSbo = kPostKc * 128;                // bytes between 8-r
 constexpr uint32_t kPostAPlane = (kRowsMax / 8) * kPostSbo;  // 20480
 constexpr uint32_t kPostBPlane = (32 / 8) * kPostSbo;        // 5120
 constexpr int kTcBarBytes = 192;  // 20 mbarriers, the TMEM address and the flags; the unit index follows
-
-// Row of the X buffer that holds pre-product row m = (i, r, re/im): rows ordered
-// (re/im, i, r), so that the B build reads (consecutive channels (r, t)) and the drain's
-// 16-byte writes (eight consecutive rows m) both hit distinct banks with a stride of 76.
-__device__ __forceinline__ int x_row(int m) {
-    const int pr = m & 1, ir = m >> 1;  // ir = i * 12 + r
-    return pr * 36 + ir;
-}
 
 // dH_j[s, t] in shared memory: rows s in blocks of 4 with 4 float2 of padding between
 // blocks, so the epilogue's three row blocks read distinct banks.
@@ -902,15 +900,18 @@ __global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restri
         *(uint4 *)(tab + base_hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
         *(uint4 *)(tab + base_lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
     }
+    // A_pre row m = 32 (r / 4) + 8 i + 4 (re/im) + r % 4 (lanes 24..31 of each quarter and
+    // the last quarter zero): one TMEM lane quarter holds every i for four r
     for (int x = tid; x < kRowsMax * 4; x += 256) {
         const int m = x >> 2, kg = x & 3;
+        const int mq = m >> 5, i = (m >> 3) & 3, pr = (m >> 2) & 1, r = 4 * mq + (m & 3);
         float v[8];
 #pragma unroll
         for (int xx = 0; xx < 8; ++xx) {
             const int kk = kg * 8 + xx;
             float val = 0.f;
-            if (m < 72 && kk < 24) {
-                const int pr = m & 1, r = (m >> 1) % 12, i = (m >> 1) / 12, pc = kk / 12, u = kk % 12;
+            if (mq < 3 && i < 3 && kk < 24) {
+                const int pc = kk / 12, u = kk % 12;
                 const float2 h = sDh[dh_at(i, r, u)];
                 val = pr ? (pc ? h.x : h.y) : (pc ? -h.y : h.x);
             }
@@ -967,8 +968,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     const int da_rows = nw + 2 * GG::DA_TE - 2;
 
     uint8_t *sB = smem + prm.off_b;              // [2 stages][re hi, re lo, im hi, im lo]
-    float *sX = (float *)(smem + prm.off_x);     // X rows (i, r, re/im) x (k', t)
-    uint8_t *sApost = smem + prm.off_b;          // epilogue: post-product A tile over the B stages and X
+    uint8_t *sApost = smem + prm.off_b;          // epilogue: post-product A tile over the B stages
     uint8_t *sBpost = smem + prm.off_bp;         // post-product B of the slot: conj(dH_j) [hi, lo]
     uint8_t *sRing = smem + prm.off_g;           // [kTcRing] pairs of re-encoded G slices
     uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
@@ -988,9 +988,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bar_tab = bars + 2 * kTcRing + 12;       // the slot's direct table copied in
     uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 13);
     static_assert((2 * kTcRing + 13) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
-    // abort flags: builders write slot g & 1 during stage g and all read it after the stage's
-    // last barrier (the next write to that slot comes after another barrier); the control
-    // warp has its own flag
+    // abort flags, each written only by its role (builders: s_abort[0]) before the unit's
+    // closing barrier and read by every thread after it
     int *s_abort = (int *)(s_tmem + 1);          // [2]
     int *s_abort_ctl = s_abort + 2;
     int *s_nvalid = s_abort + 3;
@@ -1109,8 +1108,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 // on the descriptor's low field (shared addresses stay below 2^18)
                 const uint64_t pa_h0 = smem_desc(smem_u32(sApre), 128, 512), pa_l0 = smem_desc(smem_u32(sApre) + 8192, 128, 512);
                 const uint64_t pb_h0 = smem_desc(smem_u32(sRing), 128, 512), pb_l0 = smem_desc(smem_u32(sRing) + 8192, 128, 512);
-                // pre-product of the next pair of stages: rows (i, r, re/im), N = (stage of the
-                // pair, k', t) = 128, K = (re/im of G, u)
+                // pre-product of the next pair of stages: rows (r / 4, i, re/im, r % 4), N = (stage
+                // of the pair, t / 4, k', t % 4) = 128, K = (re/im of G, u)
                 auto premma = [&]() -> bool {
                     const int slot = pair_ctr % kTcRing;
                     if (!mbar_wait_bounded(&bar_g[slot], (pair_ctr / kTcRing) & 1, kWaitNs)) return false;
@@ -1136,13 +1135,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 const uint32_t lbo_a = (uint32_t)da_rows * 16, sbo_a = 2u * lbo_a;
                 const uint32_t tstride = (uint32_t)GG::DA_GROUPS * 2 * da_rows * 16;
                 // A (direct table) at row 0 for (re/im, hi/lo); stage st starts at row nw - 1 - st + TE - 1
-                uint64_t ta[4], tb[2][4];
+                uint64_t ta[4];
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    ta[x] = smem_desc(smem_u32(sTab) + (uint32_t)x * tstride, lbo_a, sbo_a);
-                    tb[0][x] = smem_desc(smem_u32(sB) + (uint32_t)x * GG::DA_B_PLANE, 128, GG::DA_SBO_B);
-                    tb[1][x] = smem_desc(smem_u32(sB) + (uint32_t)(4 * GG::DA_B_PLANE + x * GG::DA_B_PLANE), 128, GG::DA_SBO_B);
-                }
+                for (int x = 0; x < 4; ++x) ta[x] = smem_desc(smem_u32(sTab) + (uint32_t)x * tstride, lbo_a, sbo_a);
+                // B (X of the stage) of B stage 0; stage 1 is kBufStep further, planes kPlaneStep apart
+                const uint64_t tb0 = smem_desc(smem_u32(sB), 128, GG::DA_SBO_B);
+                constexpr uint64_t kPlaneStep = GG::DA_B_PLANE >> 4, kBufStep = (4 * GG::DA_B_PLANE) >> 4;
                 const uint64_t pp_ah = smem_desc(smem_u32(sApost), 128, kPostSbo);
                 const uint64_t pp_al = smem_desc(smem_u32(sApost) + kPostAPlane, 128, kPostSbo);
                 const uint64_t pp_bh = smem_desc(smem_u32(sBpost), 128, kPostSbo);
@@ -1173,7 +1171,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const uint64_t are_h = ta[0] + r_start, are_l = ta[1] + r_start;
                     const uint64_t aim_h = ta[2] + r_start, aim_l = ta[3] + r_start;
                     const int bb = gg & 1;
-                    const uint64_t bre_h = tb[bb][0], bre_l = tb[bb][1], bim_h = tb[bb][2], bim_l = tb[bb][3];
+                    const uint64_t b0 = tb0 + (bb ? kBufStep : 0);
+                    const uint64_t bre_h = b0, bre_l = b0 + kPlaneStep, bim_h = b0 + 2 * kPlaneStep, bim_l = b0 + 3 * kPlaneStep;
                     const uint32_t dre = tmem, dim = tmem + kTcAccIm;
                     const uint32_t acc0 = job_first ? 0u : 1u;
                     // Re V = Re T Re X - Im T Im X
@@ -1281,7 +1280,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             Pos cur{t_begin, 0, 0};
             const int slot_len = (t_end - t_begin) * prm.nst;
             int o = 0;           // stage index within the slot
-            uint32_t xnext[20];  // drain warps: X of the pair's second stage, kept until then
+            uint32_t xnext[15];  // X warps: K row of the pair's second stage, kept until then
+            const int q4 = warp & 3, cb = warp >> 2;
+            const bool xw = q4 < 3;  // warps whose lane quarter holds X rows
+            // A failed wait marks this builder bad and skips its later waits; builders never
+            // leave the loop early, so every one reaches each builders_sync.
+            bool bad = false;
+            auto bwait = [&](uint64_t *bar, uint32_t parity) {
+                if (!bad && !mbar_wait_bounded(bar, parity, kWaitNs)) {
+                    bad = true;
+                    atomicExch(prm.status, 1);
+                }
+            };
             for (int g = 0; g < total; ++g, advance(cur), o = (o + 1 == slot_len) ? 0 : o + 1) {
                 const int t = cur.t, vs = cur.vs, st = cur.st;
                 const int gg = g_base + g, sb = gg & 1;
@@ -1297,87 +1307,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     }
                 }
 
-                // ---- X of this stage: TMEM rows (i, r, re/im) -> sX; at the first stage of a pair
-                // both stages are drained and the second is kept in registers ----
+                // ---- X of this stage -> B buffer sb.  Warp (lane quarter q4 < 3, column block cb)
+                // loads rows (i = 0, 1) and (i = 2, zero) of the four r of its quarter, columns
+                // (k', t) for t in [4 cb, 4 cb + 4): thread l then holds the whole K row (i, k')
+                // of B channel n = (r, t), plane re/im, with (re/im, r % 4) = l / 4 and t % 4 =
+                // l % 4.  At the first stage of a pair both stages are read, the second kept. ----
                 const bool pair_first = (o & 1) == 0;
                 if (pair_first) {
-                    if (!mbar_wait_bounded(bar_pre, pair_ctr & 1, kWaitNs)) {
-                        s_abort[sb] = 1;
-                        atomicExch(prm.status, 1);
-                    }
+                    bwait(bar_pre, pair_ctr & 1);
                     ++pair_ctr;
                     tc_fence_after();
                 }
-                if ((warp & 3) < 3) {
-                    const int cb = warp >> 2;  // 20-column block of the 60 columns (k', t)
-                    const int m = (warp & 3) * 32 + lane;
-                    uint32_t xr[20];
+                uint32_t xa[10], xb[10];  // rows (i0 | i1) and (i2 | zero), repetition k = k'
+                if (xw) {
                     if (pair_first) {
-                        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + kTcPre + 20 * cb;
-                        tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(xr));
-                        tmem_ld4(taddr + 16, *reinterpret_cast<uint32_t(*)[4]>(xr + 16));
-                        tmem_ld16(taddr + 64, *reinterpret_cast<uint32_t(*)[16]>(xnext));
-                        tmem_ld4(taddr + 64 + 16, *reinterpret_cast<uint32_t(*)[4]>(xnext + 16));
+                        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + kTcPre + 20 * cb;
+                        using R8 = uint32_t(&)[8];
+                        using R2 = uint32_t(&)[2];
+                        tmem_ld16x128_x4(ta, reinterpret_cast<R8>(xa[0]));
+                        tmem_ld16x128_x1(ta + 16, reinterpret_cast<R2>(xa[8]));
+                        tmem_ld16x128_x4(ta + (16u << 16), reinterpret_cast<R8>(xb[0]));
+                        tmem_ld16x128_x1(ta + (16u << 16) + 16, reinterpret_cast<R2>(xb[8]));
+                        uint32_t na[10], nb[10];
+                        tmem_ld16x128_x4(ta + 64, reinterpret_cast<R8>(na[0]));
+                        tmem_ld16x128_x1(ta + 64 + 16, reinterpret_cast<R2>(na[8]));
+                        tmem_ld16x128_x4(ta + 64 + (16u << 16), reinterpret_cast<R8>(nb[0]));
+                        tmem_ld16x128_x1(ta + 64 + (16u << 16) + 16, reinterpret_cast<R2>(nb[8]));
                         tmem_ld_wait();
                         tc_fence_before();
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            xnext[k] = na[2 * k];
+                            xnext[5 + k] = na[2 * k + 1];
+                            xnext[10 + k] = nb[2 * k];
+                        }
                     } else {
 #pragma unroll
-                        for (int x = 0; x < 20; ++x) xr[x] = xnext[x];
-                    }
-                    if (m < 72) {
-                        float4 *row = (float4 *)(sX + x_row(m) * kXs + 20 * cb);
-#pragma unroll
-                        for (int x = 0; x < 5; ++x)
-                            row[x] = make_float4(__uint_as_float(xr[4 * x]), __uint_as_float(xr[4 * x + 1]),
-                                                 __uint_as_float(xr[4 * x + 2]), __uint_as_float(xr[4 * x + 3]));
-                    }
-                }
-                builders_sync();
-                // ---- the B buffer must be free: main MMAs of stage g - 2 complete ----
-                if (gg >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((gg >> 1) - 1) & 1, kWaitNs)) {
-                    s_abort[sb] = 1;
-                    atomicExch(prm.status, 1);
-                }
-                // ---- X -> B planes [re, im][hi, lo] of channel n = (r, t), K index i * Nkz + k' ----
-                uint8_t *bda = sB + sb * (4 * GG::DA_B_PLANE);
-                for (int item = tid; item < 2 * kCh; item += kTcBuilders) {
-                    const int n = item % kCh, pr = item / kCh, r = n / 12, tt = n % 12;
-                    float xv[16];
-#pragma unroll
-                    for (int kk = 0; kk < 16; ++kk) {
-                        xv[kk] = 0.f;
-                        if (kk < 3 * NK) {
-                            const int i = kk / NK, kp = kk % NK;
-                            xv[kk] = sX[x_row((i * 12 + r) * 2 + pr) * kXs + kp * 12 + tt];
+                        for (int k = 0; k < 5; ++k) {
+                            xa[2 * k] = xnext[k];
+                            xa[2 * k + 1] = xnext[5 + k];
+                            xb[2 * k] = xnext[10 + k];
                         }
                     }
+                }
+                // ---- the B buffer must be free: main MMAs of stage g - 2 complete ----
+                if (gg >= 2) bwait(&bar_mma[sb], ((gg >> 1) - 1) & 1);
+                if (xw) {
+                    // K row kk = i * Nkz + k' (15 used, 16th zero), split into bf16 hi / lo
+                    float v[16];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        v[k] = __uint_as_float(xa[2 * k]);
+                        v[5 + k] = __uint_as_float(xa[2 * k + 1]);
+                        v[10 + k] = __uint_as_float(xb[2 * k]);
+                    }
+                    v[15] = 0.f;
                     uint32_t hv[8], lv[8];
 #pragma unroll
                     for (int x = 0; x < 8; ++x) {
-                        const uint2 hl = split2_bf16(xv[2 * x], xv[2 * x + 1]);
+                        const uint2 hl = split2_bf16(v[2 * x], v[2 * x + 1]);
                         hv[x] = hl.x;
                         lv[x] = hl.y;
                     }
-                    const uint32_t row_off = (n >> 3) * GG::DA_SBO_B + (n & 7) * 16;
-                    uint8_t *ph = bda + (2 * pr) * GG::DA_B_PLANE, *pl = ph + GG::DA_B_PLANE;
-#pragma unroll
-                    for (int gq = 0; gq < 2; ++gq) {
-                        *(uint4 *)(ph + row_off + gq * 128) = make_uint4(hv[4 * gq], hv[4 * gq + 1], hv[4 * gq + 2], hv[4 * gq + 3]);
-                        *(uint4 *)(pl + row_off + gq * 128) = make_uint4(lv[4 * gq], lv[4 * gq + 1], lv[4 * gq + 2], lv[4 * gq + 3]);
-                    }
+                    const int pr = lane >> 4, n = (4 * q4 + ((lane >> 2) & 3)) * 12 + 4 * cb + (lane & 3);
+                    uint8_t *ph = sB + sb * (4 * GG::DA_B_PLANE) + (2 * pr) * GG::DA_B_PLANE + (n >> 3) * GG::DA_SBO_B +
+                                  (n & 7) * 16;
+                    *(uint4 *)ph = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    *(uint4 *)(ph + 128) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
+                    *(uint4 *)(ph + GG::DA_B_PLANE) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    *(uint4 *)(ph + GG::DA_B_PLANE + 128) = make_uint4(lv[4], lv[5], lv[6], lv[7]);
                 }
                 fence_proxy_async_smem();
                 mbar_arrive(&bar_bready[sb]);
 
                 if (job_last) {
                     // ---- epilogue of the job: Sigma += sum_j V_j dH_j^dagger (V = acc_re + i acc_im) ----
-                    if (!mbar_wait_bounded(bar_job, job_ctr & 1, kWaitNs)) {
-                        s_abort[sb] = 1;
-                        atomicExch(prm.status, 1);
-                    }
+                    bwait(bar_job, job_ctr & 1);
                     ++job_ctr;
                     tc_fence_after();
-                    builders_sync();  // every builder is done with X and B before the A tile overlays them
+                    builders_sync();  // every builder is done with B before the A tile overlays it
                     const bool first_slot = vs == 0, last_slot = vs == nvalid - 1;
                     // A-tile role: warp -> (lane quarter, row r' of the tile); lane -> accumulator row
                     const int aq = warp & 3, arl = warp >> 2;
@@ -1405,10 +1413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         }
                         if (q > 0) {
                             // MMAs of tile q - 1 done: its result can be drained, the A tile reused
-                            if (!mbar_wait_bounded(&bar_post[(tq - 1) & 1], ((tq - 1) >> 1) & 1, kWaitNs)) {
-                                s_abort[sb] = 1;
-                                atomicExch(prm.status, 1);
-                            }
+                            bwait(&bar_post[(tq - 1) & 1], ((tq - 1) >> 1) & 1);
                             tc_fence_after();
                         }
                         tmem_ld_wait();
@@ -1474,9 +1479,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     }
                     tile_ctr += 4;
                 }
-                builders_sync();
-                if (s_abort[sb]) break;
             }
+            if (bad) s_abort[0] = 1;  // read by every thread after the unit's closing barrier
         }
         g_base += total;
         __syncthreads();
@@ -1504,9 +1508,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// Shared memory of the warp-specialised kernel: B stages and the X buffer (the epilogue's
-// drained accumulators overlay both), the G-slice ring, the pre-product's dH operand, the
-// direct table, dH and the barriers.
+// Shared memory of the warp-specialised kernel: the two B stages (the epilogue's post-product
+// A tile overlays them), the G-slice ring, the pre-product's dH operand, the direct table,
+// the post-product's conj(dH) operand and the barriers.
 uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
     using GG = Geo<5>;
     uint32_t off = 0;
@@ -1517,9 +1521,9 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
         return at;
     };
     const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
-    const uint32_t bx = bsz + 72 * kXs * 4, nv = 2 * kPostAPlane;
-    prm.off_b = take(bx > nv ? bx : nv, 1024);
-    prm.off_x = prm.off_b + bsz;
+    const uint32_t nv = 2 * kPostAPlane;
+    prm.off_b = take(bsz > nv ? bsz : nv, 1024);
+    prm.off_x = 0;
     prm.off_g = take(kTcRing * kTcPairBytes, 1024);
     prm.off_a = take(2 * 8192, 1024);
     const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
@@ -1642,6 +1646,7 @@ sse_status split_g(const Plan &p, const sse_io &io, cudaStream_t st) {
     const void *gs[2] = {io.S_gt ? io.G_gt : nullptr, io.S_lt ? io.G_lt : nullptr};
     const void *ds[2] = {io.D_gt, io.D_lt};
     const uint32_t tsmem = 3 * kDhJ * 8 + 5 * p.d.nw * 9 * 8;
+    if (p.d.nkz != 5) return set_error("mixed mode: the tensor-core form needs Nkz = 5"), SSE_E_INVALID_ARG;
     for (int s = 0; s < 2; ++s) {
         if (!gs[s]) continue;
         const long long slices = (long long)p.d.ne * p.d.na;

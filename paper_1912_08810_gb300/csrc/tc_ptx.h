@@ -155,6 +155,18 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
+// 16 lanes x 4 columns per repetition (lane base a multiple of 16 inside the warp's lane
+// quarter): thread t gets, for repetition k, r[2k] from lane (base + t / 4) and r[2k + 1]
+// from lane (base + 8 + t / 4), both at column (base + 4k + t % 4).
+__device__ __forceinline__ void tmem_ld16x128_x4(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.16x128b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16x128_x1(uint32_t taddr, uint32_t (&r)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.16x128b.x1.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+}
+
 // 32 lanes x 8 columns of 32-bit values: thread t of the warp gets lane (base + t).
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
