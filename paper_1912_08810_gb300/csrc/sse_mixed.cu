@@ -796,21 +796,26 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // ---- the tensor-core form with the pre-product (Nkz = 5), warp-specialised ---------------
 //
 // Same arithmetic as the direct form above with X = dH_i . G taken from the tensor cores,
-// but the CTA is split by role so that the MMAs of one stage run while the next stage is
-// prepared: eight builder warps (slot tables, X drain, B operand, epilogue) and one control
-// warp whose lane 0 issues the bulk copies of the G slices and every MMA.  Hand-offs go
-// through mbarriers: builders -> control "B of stage g ready" and "slot tables ready";
-// control -> builders through MMA commits ("X of stage g ready", "job accumulated").  A
-// third role, one more warp, streams the G slices into a ring of four; the control warp
-// hands a ring slot back with an MMA commit once the pre-product that read it is done.
-// The pre-product runs for two stages at once (N = 128: the two G slices side by side), as
-// soon as the builders have drained the previous pair (at its first stage), ahead of the
-// main MMAs, so the builders rarely wait for X while the tensor pipe has work.  The product with dH_j^dagger at the end of a
-// job runs on the tensor cores too: the builders re-encode the accumulators tile by tile
-// (bf16 hi / lo, three products as elsewhere) and the control warp issues its MMAs.
-constexpr int kTcBuilders = 384;
-constexpr int kTcThreads = kTcBuilders + 64;  // + control warp + bulk-copy warp
+// but the CTA is split by role so that the MMAs of one stage run while the next ones are
+// prepared.  Twelve builder warps: nine of them turn the pre-product X in TMEM into the main
+// MMAs' B operand of each stage, all twelve run the epilogue of a job (the product with
+// dH_j^dagger, also on the tensor cores: the builders re-encode the accumulators tile by
+// tile as bf16 hi / lo and the control warp issues its MMAs).  One control warp, whose lane
+// 0 issues every MMA, on the scheduler the three builder warps without stage work share
+// (they sleep at a hardware barrier between epilogues).  One bulk-copy warp streams the G
+// slices into a ring and the slot tables into shared memory.  Hand-offs go through
+// mbarriers: builders -> control "B of stage g built", "post-product tile built"; control
+// -> builders through MMA commits ("X of a pair ready", "B buffer free", "job accumulated");
+// the copies complete their own barriers.  The pre-product runs for two stages at once
+// (N = 128: the two G slices side by side) as soon as the builders have read the previous
+// pair (at its first stage), ahead of the main MMAs.
+constexpr int kTcBuilders = 384;            // warps 0..11
+constexpr int kTcXBuilders = 288;           // warps whose lane quarter holds X rows (warp % 4 < 3)
+constexpr int kTcPrdWarp = 13;              // bulk copies
+constexpr int kTcCtlWarp = 15;              // MMA issue; warps 12 and 14 only take part in the CTA barriers
+constexpr int kTcThreads = 512;
 constexpr int kTcRing = 2;   // pairs of G slices in flight
+constexpr int kTcBStages = 3;  // B operands in flight: builders run up to two stages ahead of the MMAs
 constexpr uint32_t kTcPairBytes = 16384;  // one ring slot: two slices, [hi s0 | hi s1 | lo s0 | lo s1]
 // TMEM columns of the warp-specialised kernel
 constexpr uint32_t kTcAccIm = 160;             // Im V (Re V at 0), 144 columns each
@@ -961,8 +966,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     using GG = Geo<NK>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool ctl = warp == kTcBuilders / 32;      // control warp
-    const bool prd = warp == kTcBuilders / 32 + 1;  // bulk-copy warp
+    const bool ctl = warp == kTcCtlWarp;  // control warp
+    const bool prd = warp == kTcPrdWarp;  // bulk-copy warp
     const int nw = prm.nw;
     const int omega_max = prm.omega_first + nw - 1;
     const int da_rows = nw + 2 * GG::DA_TE - 2;
@@ -974,20 +979,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
     uint8_t *sTab = smem + prm.off_df;           // direct Toeplitz table of the slot
     uint64_t *bars = (uint64_t *)(smem + prm.off_bar);
-    uint64_t *bar_g = bars;                      // [kTcRing] pair of slices landed
-    uint64_t *bar_pre = bars + kTcRing;          // pre-product of a pair done
-    uint64_t *bar_bready = bars + kTcRing + 1;   // [2] B of a stage built
-    uint64_t *bar_job = bars + kTcRing + 3;      // last MMAs of a job done
-    uint64_t *bar_slot = bars + kTcRing + 4;     // the slot's pre- and post-product operands copied in
-    uint64_t *bar_fin = bars + kTcRing + 5;      // abort: every MMA issued so far done
-    uint64_t *bar_mma = bars + kTcRing + 6;      // [2] main MMAs of a stage done (B buffer free)
-    uint64_t *bar_apost = bars + kTcRing + 8;    // post-product A tile built
-    uint64_t *bar_post = bars + kTcRing + 9;     // [2] post-product MMAs of a tile done
-    uint64_t *bar_empty = bars + kTcRing + 11;   // [kTcRing] pre-product done with a ring slot
-    uint64_t *bar_slotfree = bars + 2 * kTcRing + 11;  // every MMA of the previous slot done
-    uint64_t *bar_tab = bars + 2 * kTcRing + 12;       // the slot's direct table copied in
-    uint32_t *s_tmem = (uint32_t *)(bars + 2 * kTcRing + 13);
-    static_assert((2 * kTcRing + 13) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
+    uint64_t *bar_g = bars;                          // [kTcRing] pair of slices landed
+    uint64_t *bar_empty = bar_g + kTcRing;           // [kTcRing] pre-product done with a ring slot
+    uint64_t *bar_bready = bar_empty + kTcRing;      // [kTcBStages] B of a stage built
+    uint64_t *bar_mma = bar_bready + kTcBStages;     // [kTcBStages] main MMAs of a stage done (B free)
+    uint64_t *bar_post = bar_mma + kTcBStages;       // [2] post-product MMAs of a tile done
+    uint64_t *bar_pre = bar_post + 2;                // pre-product of a pair done
+    uint64_t *bar_job = bar_pre + 1;                 // last MMAs of a job done
+    uint64_t *bar_slot = bar_job + 1;                // the slot's pre- and post-product operands copied in
+    uint64_t *bar_fin = bar_slot + 1;                // abort: every MMA issued so far done
+    uint64_t *bar_apost = bar_fin + 1;               // post-product A tile built
+    uint64_t *bar_slotfree = bar_apost + 1;          // every MMA of the previous slot done
+    uint64_t *bar_tab = bar_slotfree + 1;            // the slot's direct table copied in
+    uint32_t *s_tmem = (uint32_t *)(bar_tab + 1);
+    static_assert((2 * kTcRing + 2 * kTcBStages + 9) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
     // abort flags, each written only by its role (builders: s_abort[0]) before the unit's
     // closing barrier and read by every thread after it
     int *s_abort = (int *)(s_tmem + 1);          // [2]
@@ -1001,15 +1006,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (tid == 0) {
         for (int b = 0; b < kTcRing; ++b) mbar_init(&bar_g[b], 1);
         mbar_init(bar_pre, 1);
-        mbar_init(&bar_bready[0], kTcBuilders);
-        mbar_init(&bar_bready[1], kTcBuilders);
+        for (int b = 0; b < kTcBStages; ++b) {
+            mbar_init(&bar_bready[b], kTcXBuilders);
+            mbar_init(&bar_mma[b], 1);
+        }
         mbar_init(bar_job, 1);
         mbar_init(bar_slot, 1);
         mbar_init(bar_tab, 1);
         mbar_init(bar_slotfree, 1);
         mbar_init(bar_fin, 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
         mbar_init(bar_apost, kTcBuilders);
         mbar_init(&bar_post[0], 1);
         mbar_init(&bar_post[1], 1);
@@ -1157,7 +1162,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         tc_fence_after();
                         if (!(ok = premma())) break;
                     }
-                    if (!(ok = mbar_wait_bounded(&bar_bready[gg & 1], (gg >> 1) & 1, kWaitNs))) break;
+                    const int bb = gg % kTcBStages, use = gg / kTcBStages;  // B buffer and its use count
+                    if (!(ok = mbar_wait_bounded(&bar_bready[bb], use & 1, kWaitNs))) break;
                     if (o == 0) {
                         ok = mbar_wait_bounded(bar_tab, slot_ctr & 1, kWaitNs);
                         ++slot_ctr;
@@ -1170,8 +1176,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const uint64_t r_start = (uint64_t)(nw - 1 - m.st + GG::DA_TE - 1);
                     const uint64_t are_h = ta[0] + r_start, are_l = ta[1] + r_start;
                     const uint64_t aim_h = ta[2] + r_start, aim_l = ta[3] + r_start;
-                    const int bb = gg & 1;
-                    const uint64_t b0 = tb0 + (bb ? kBufStep : 0);
+                    const uint64_t b0 = tb0 + (uint64_t)bb * kBufStep;
                     const uint64_t bre_h = b0, bre_l = b0 + kPlaneStep, bim_h = b0 + 2 * kPlaneStep, bim_l = b0 + 3 * kPlaneStep;
                     const uint32_t dre = tmem, dim = tmem + kTcAccIm;
                     const uint32_t acc0 = job_first ? 0u : 1u;
@@ -1275,7 +1280,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 }
             }
             __syncwarp();
-        } else {
+        } else if (warp < kTcBuilders / 32) {
             // ================= builder warps =================
             Pos cur{t_begin, 0, 0};
             const int slot_len = (t_end - t_begin) * prm.nst;
@@ -1287,14 +1292,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             // leave the loop early, so every one reaches each builders_sync.
             bool bad = false;
             auto bwait = [&](uint64_t *bar, uint32_t parity) {
-                if (!bad && !mbar_wait_bounded(bar, parity, kWaitNs)) {
+                if (!bad && !mbar_wait_bounded_sleep(bar, parity, kWaitNs)) {
                     bad = true;
                     atomicExch(prm.status, 1);
                 }
             };
             for (int g = 0; g < total; ++g, advance(cur), o = (o + 1 == slot_len) ? 0 : o + 1) {
                 const int t = cur.t, vs = cur.vs, st = cur.st;
-                const int gg = g_base + g, sb = gg & 1;
+                const int gg = g_base + g, sb = gg % kTcBStages, use = gg / kTcBStages;
                 const int E0 = t * GG::TE;
                 const bool job_first = st == 0, job_last = st == prm.nst - 1;
                 if (job_first && vs > 0) {
@@ -1313,11 +1318,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 // of B channel n = (r, t), plane re/im, with (re/im, r % 4) = l / 4 and t % 4 =
                 // l % 4.  At the first stage of a pair both stages are read, the second kept. ----
                 const bool pair_first = (o & 1) == 0;
-                if (pair_first) {
+                if (pair_first && xw) {
                     bwait(bar_pre, pair_ctr & 1);
-                    ++pair_ctr;
                     tc_fence_after();
                 }
+                if (pair_first) ++pair_ctr;
                 uint32_t xa[10], xb[10];  // rows (i0 | i1) and (i2 | zero), repetition k = k'
                 if (xw) {
                     if (pair_first) {
@@ -1350,8 +1355,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         }
                     }
                 }
-                // ---- the B buffer must be free: main MMAs of stage g - 2 complete ----
-                if (gg >= 2) bwait(&bar_mma[sb], ((gg >> 1) - 1) & 1);
+                // ---- the B buffer must be free: the main MMAs of its previous stage complete ----
+                if (xw && use > 0) bwait(&bar_mma[sb], (use - 1) & 1);
                 if (xw) {
                     // K row kk = i * Nkz + k' (15 used, 16th zero), split into bf16 hi / lo
                     float v[16];
@@ -1377,15 +1382,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     *(uint4 *)(ph + GG::DA_B_PLANE) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     *(uint4 *)(ph + GG::DA_B_PLANE + 128) = make_uint4(lv[4], lv[5], lv[6], lv[7]);
                 }
-                fence_proxy_async_smem();
-                mbar_arrive(&bar_bready[sb]);
+                if (xw) {
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bar_bready[sb]);
+                }
 
                 if (job_last) {
                     // ---- epilogue of the job: Sigma += sum_j V_j dH_j^dagger (V = acc_re + i acc_im) ----
-                    bwait(bar_job, job_ctr & 1);
+                    // the X warps see the job's MMAs done; the others (no stage work) sleep at the
+                    // barrier until then
+                    if (xw) bwait(bar_job, job_ctr & 1);
                     ++job_ctr;
-                    tc_fence_after();
                     builders_sync();  // every builder is done with B before the A tile overlays it
+                    tc_fence_after();
                     const bool first_slot = vs == 0, last_slot = vs == nvalid - 1;
                     // A-tile role: warp -> (lane quarter, row r' of the tile); lane -> accumulator row
                     const int aq = warp & 3, arl = warp >> 2;
@@ -1508,7 +1517,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// Shared memory of the warp-specialised kernel: the two B stages (the epilogue's post-product
+// Shared memory of the warp-specialised kernel: the B stages (the epilogue's post-product
 // A tile overlays them), the G-slice ring, the pre-product's dH operand, the direct table,
 // the post-product's conj(dH) operand and the barriers.
 uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
@@ -1520,7 +1529,7 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
         off += bytes;
         return at;
     };
-    const uint32_t bsz = 2 * 4 * GG::DA_B_PLANE;
+    const uint32_t bsz = kTcBStages * 4 * GG::DA_B_PLANE;
     const uint32_t nv = 2 * kPostAPlane;
     prm.off_b = take(bsz > nv ? bsz : nv, 1024);
     prm.off_x = 0;
