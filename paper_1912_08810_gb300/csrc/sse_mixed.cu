@@ -815,7 +815,7 @@ constexpr int kTcPrdWarp = 13;              // bulk copies
 constexpr int kTcCtlWarp = 15;              // MMA issue; warps 12 and 14 only take part in the CTA barriers
 constexpr int kTcThreads = 512;
 constexpr int kTcRing = 2;   // pairs of G slices in flight
-constexpr int kTcBStages = 3;  // B operands in flight: builders run up to two stages ahead of the MMAs
+constexpr int kTcBStages = 2;  // B operands in flight: builders build stage g + 1 while the MMAs of stage g run
 constexpr uint32_t kTcPairBytes = 16384;  // one ring slot: two slices, [hi s0 | hi s1 | lo s0 | lo s1]
 // TMEM columns of the warp-specialised kernel
 constexpr uint32_t kTcAccIm = 160;             // Im V (Re V at 0), 144 columns each

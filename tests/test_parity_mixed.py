@@ -48,6 +48,8 @@ def test_every_supported_nkz(nkz):
     dict(nkz=2, nqz=2, ne=5, nw=9, na=6, nb=2, omega_first=2),    # most E - omega below the grid
     dict(nkz=1, nqz=1, ne=70, nw=16, na=1, nb=4, omega_first=1),  # one atom, self slots
     dict(nkz=5, nqz=5, ne=17, nw=32, na=3, nb=4, omega_first=1),  # Nw = 32 with a short grid
+    dict(nkz=5, nqz=5, ne=21, nw=50, na=2, nb=2, omega_first=1),  # largest Nw of the warp-specialised form
+    dict(nkz=5, nqz=5, ne=21, nw=56, na=2, nb=2, omega_first=1),  # past it: the single-role form takes over
 ])
 def test_edge_geometries(case):
     of = case.pop("omega_first")
