@@ -800,9 +800,13 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // prepared.  Twelve builder warps: nine of them turn the pre-product X in TMEM into the main
 // MMAs' B operand of each stage, all twelve run the epilogue of a job (the product with
 // dH_j^dagger, also on the tensor cores: the builders re-encode the accumulators tile by
-// tile as bf16 hi / lo and the control warp issues its MMAs).  One control warp, whose lane
-// 0 issues every MMA, on the scheduler the three builder warps without stage work share
-// (they sleep at a hardware barrier between epilogues).  One bulk-copy warp streams the G
+// tile as bf16 hi / lo and the control warp issues its MMAs).  Two MMA-issuing warps (lane
+// 0 of each): one issues the MMAs into Re V, the pre-product and the post-product, the other
+// the MMAs into Im V, so that one issuer's bookkeeping between stages hides behind the other's
+// queued MMAs (an issuing thread blocks while the tensor pipe's queue is full, and its MMAs
+// complete in its own issue order; the two write disjoint accumulators).  The first sits on
+// the scheduler of the three builder warps without stage work (they sleep at a hardware
+// barrier between epilogues).  One bulk-copy warp streams the G
 // slices into a ring and the slot tables into shared memory.  Hand-offs go through
 // mbarriers: builders -> control "B of stage g built", "post-product tile built"; control
 // -> builders through MMA commits ("X of a pair ready", "B buffer free", "job accumulated");
@@ -812,7 +816,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 constexpr int kTcBuilders = 384;            // warps 0..11
 constexpr int kTcXBuilders = 288;           // warps whose lane quarter holds X rows (warp % 4 < 3)
 constexpr int kTcPrdWarp = 13;              // bulk copies
-constexpr int kTcCtlWarp = 15;              // MMA issue; warps 12 and 14 only take part in the CTA barriers
+constexpr int kTcCtlWarp = 15;              // MMAs into Re V, the pre- and the post-product
+constexpr int kTcCtl2Warp = 14;             // MMAs into Im V; warp 12 only takes part in the CTA barriers
 constexpr int kTcThreads = 512;
 constexpr int kTcRing = 2;   // pairs of G slices in flight
 constexpr int kTcBStages = 2;  // B operands in flight: builders build stage g + 1 while the MMAs of stage g run
@@ -966,8 +971,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     using GG = Geo<NK>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool ctl = warp == kTcCtlWarp;  // control warp
-    const bool prd = warp == kTcPrdWarp;  // bulk-copy warp
+    const bool ctl = warp == kTcCtlWarp || warp == kTcCtl2Warp;  // MMA-issuing warps
+    const bool re_side = warp == kTcCtlWarp;                      // Re V, pre- and post-product
+    const bool prd = warp == kTcPrdWarp;                          // bulk-copy warp
     const int nw = prm.nw;
     const int omega_max = prm.omega_first + nw - 1;
     const int da_rows = nw + 2 * GG::DA_TE - 2;
@@ -1008,13 +1014,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(bar_pre, 1);
         for (int b = 0; b < kTcBStages; ++b) {
             mbar_init(&bar_bready[b], kTcXBuilders);
-            mbar_init(&bar_mma[b], 1);
+            mbar_init(&bar_mma[b], 2);  // a commit from each issuing warp
         }
-        mbar_init(bar_job, 1);
+        mbar_init(bar_job, 2);       // both issuing warps
         mbar_init(bar_slot, 1);
         mbar_init(bar_tab, 1);
-        mbar_init(bar_slotfree, 1);
-        mbar_init(bar_fin, 1);
+        mbar_init(bar_slotfree, 2);  // both issuing warps
+        mbar_init(bar_fin, 2);       // both issuing warps
         mbar_init(bar_apost, kTcBuilders);
         mbar_init(&bar_post[0], 1);
         mbar_init(&bar_post[1], 1);
@@ -1157,7 +1163,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const int gg = g_base + g;
                     const bool job_first = m.st == 0, job_last = m.st == prm.nst - 1;
                     const int slot_rem = slot_len - 1 - o;  // stages after this one in its slot
-                    if (o == 0) {
+                    if (o == 0 && re_side) {
                         if (!(ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs))) break;
                         tc_fence_after();
                         if (!(ok = premma())) break;
@@ -1172,7 +1178,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     tc_fence_after();
                     // X of the next pair ahead of this stage's main MMAs: the builders drained the
                     // TMEM buffer at this (first) stage of the current pair
-                    if ((o & 1) == 0 && slot_rem >= 2 && !(ok = premma())) break;
+                    if (re_side && (o & 1) == 0 && slot_rem >= 2 && !(ok = premma())) break;
                     const uint64_t r_start = (uint64_t)(nw - 1 - m.st + GG::DA_TE - 1);
                     const uint64_t are_h = ta[0] + r_start, are_l = ta[1] + r_start;
                     const uint64_t aim_h = ta[2] + r_start, aim_l = ta[3] + r_start;
@@ -1180,22 +1186,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const uint64_t bre_h = b0, bre_l = b0 + kPlaneStep, bim_h = b0 + 2 * kPlaneStep, bim_l = b0 + 3 * kPlaneStep;
                     const uint32_t dre = tmem, dim = tmem + kTcAccIm;
                     const uint32_t acc0 = job_first ? 0u : 1u;
-                    // Re V = Re T Re X - Im T Im X
-                    mma_ss(dre, are_h, bre_h, idesc, acc0);
-                    mma_ss(dre, are_h, bre_l, idesc, 1u);
-                    mma_ss(dre, are_l, bre_h, idesc, 1u);
-                    mma_ss(dre, aim_h, bim_h, idesc_negb, 1u);
-                    mma_ss(dre, aim_h, bim_l, idesc_negb, 1u);
-                    mma_ss(dre, aim_l, bim_h, idesc_negb, 1u);
-                    // Im V = Im T Re X + Re T Im X
-                    mma_ss(dim, aim_h, bre_h, idesc, acc0);
-                    mma_ss(dim, aim_h, bre_l, idesc, 1u);
-                    mma_ss(dim, aim_l, bre_h, idesc, 1u);
-                    mma_ss(dim, are_h, bim_h, idesc, 1u);
-                    mma_ss(dim, are_h, bim_l, idesc, 1u);
-                    mma_ss(dim, are_l, bim_h, idesc, 1u);
+                    if (re_side) {
+                        // Re V = Re T Re X - Im T Im X
+                        mma_ss(dre, are_h, bre_h, idesc, acc0);
+                        mma_ss(dre, are_h, bre_l, idesc, 1u);
+                        mma_ss(dre, are_l, bre_h, idesc, 1u);
+                        mma_ss(dre, aim_h, bim_h, idesc_negb, 1u);
+                        mma_ss(dre, aim_h, bim_l, idesc_negb, 1u);
+                        mma_ss(dre, aim_l, bim_h, idesc_negb, 1u);
+                    } else {
+                        // Im V = Im T Re X + Re T Im X
+                        mma_ss(dim, aim_h, bre_h, idesc, acc0);
+                        mma_ss(dim, aim_h, bre_l, idesc, 1u);
+                        mma_ss(dim, aim_l, bre_h, idesc, 1u);
+                        mma_ss(dim, are_h, bim_h, idesc, 1u);
+                        mma_ss(dim, are_h, bim_l, idesc, 1u);
+                        mma_ss(dim, are_l, bim_h, idesc, 1u);
+                    }
                     mma_commit(&bar_mma[bb]);
-                    if (job_last) {
+                    if (job_last && !re_side) {
+                        mma_commit(bar_job);
+                        if (slot_rem == 0) mma_commit(bar_slotfree);
+                    }
+                    if (job_last && re_side) {
                         mma_commit(bar_job);
                         // post-product of the job, one M tile at a time as the builders fill it
                         constexpr uint32_t idesc_p = idesc_bf16_f32(kRowsMax, 32);
