@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // prepared.  Twelve builder warps: nine of them turn the pre-product X in TMEM into the main
 // MMAs' B operand of each stage, all twelve run the epilogue of a job (the product with
 // dH_j^dagger, also on the tensor cores: the builders re-encode the accumulators tile by
-// tile as bf16 hi / lo and the control warp issues its MMAs).  Two MMA-issuing warps (lane
+// tile as bf16 hi / lo and an MMA-issuing warp issues its MMAs).  Two MMA-issuing warps (lane
 // 0 of each): one issues the MMAs into Re V, the pre-product and the post-product, the other
 // the MMAs into Im V, so that one issuer's bookkeeping between stages hides behind the other's
 // queued MMAs (an issuing thread blocks while the tensor pipe's queue is full, and its MMAs
@@ -1113,7 +1113,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         };
 
         if (ctl) {
-            // ================= control warp: bulk copies and MMAs (lane 0) =================
+            // ================= MMA-issuing warps (lane 0): Re side and Im side =================
             if (lane == 0) {
                 // descriptors: fixed parts built once; a shift of the start address is an add
                 // on the descriptor's low field (shared addresses stay below 2^18)
