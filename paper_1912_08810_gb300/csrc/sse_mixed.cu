@@ -800,11 +800,11 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // prepared.  Twelve builder warps: nine of them turn the pre-product X in TMEM into the main
 // MMAs' B operand of each stage, all twelve run the epilogue of a job (the product with
 // dH_j^dagger, also on the tensor cores: the builders re-encode the accumulators tile by
-// tile as bf16 hi / lo and an MMA-issuing warp issues its MMAs).  Two MMA-issuing warps (lane
-// 0 of each): one issues the MMAs into Re V, the pre-product and the post-product, the other
-// the MMAs into Im V, so that one issuer's bookkeeping between stages hides behind the other's
-// queued MMAs (an issuing thread blocks while the tensor pipe's queue is full, and its MMAs
-// complete in its own issue order; the two write disjoint accumulators).  The first sits on
+// tile as bf16 hi / lo and an MMA-issuing warp issues its MMAs).  Three MMA-issuing warps
+// (lane 0 of each): one issues the MMAs into Re V and the post-product, one the MMAs into
+// Im V, one the pre-product, so that one issuer's bookkeeping between stages hides behind the
+// others' queued MMAs (an issuing thread blocks while the tensor pipe's queue is full, and its
+// MMAs complete in its own issue order; the three write disjoint accumulators).  The first sits on
 // the scheduler of the three builder warps without stage work (they sleep at a hardware
 // barrier between epilogues).  One bulk-copy warp streams the G
 // slices into a ring and the slot tables into shared memory.  Hand-offs go through
@@ -816,8 +816,9 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 constexpr int kTcBuilders = 384;            // warps 0..11
 constexpr int kTcXBuilders = 288;           // warps whose lane quarter holds X rows (warp % 4 < 3)
 constexpr int kTcPrdWarp = 13;              // bulk copies
-constexpr int kTcCtlWarp = 15;              // MMAs into Re V, the pre- and the post-product
-constexpr int kTcCtl2Warp = 14;             // MMAs into Im V; warp 12 only takes part in the CTA barriers
+constexpr int kTcCtlWarp = 15;              // MMAs into Re V and the post-product
+constexpr int kTcCtl2Warp = 14;             // MMAs into Im V
+constexpr int kTcPreWarp = 12;              // the pre-product
 constexpr int kTcThreads = 512;
 constexpr int kTcRing = 2;   // pairs of G slices in flight
 constexpr int kTcBStages = 2;  // B operands in flight: builders build stage g + 1 while the MMAs of stage g run
@@ -971,8 +972,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     using GG = Geo<NK>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool ctl = warp == kTcCtlWarp || warp == kTcCtl2Warp;  // MMA-issuing warps
-    const bool re_side = warp == kTcCtlWarp;                      // Re V, pre- and post-product
+    const bool ctl = warp == kTcCtlWarp || warp == kTcCtl2Warp || warp == kTcPreWarp;  // MMA-issuing warps
+    const bool re_side = warp == kTcCtlWarp;   // main MMAs into Re V, the post-product
+    const bool im_side = warp == kTcCtl2Warp;  // main MMAs into Im V
+    const bool pre_side = warp == kTcPreWarp;  // the pre-product
     const bool prd = warp == kTcPrdWarp;                          // bulk-copy warp
     const int nw = prm.nw;
     const int omega_max = prm.omega_first + nw - 1;
@@ -1019,8 +1022,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(bar_job, 2);       // both issuing warps
         mbar_init(bar_slot, 1);
         mbar_init(bar_tab, 1);
-        mbar_init(bar_slotfree, 2);  // both issuing warps
-        mbar_init(bar_fin, 2);       // both issuing warps
+        mbar_init(bar_slotfree, 3);  // the three issuing warps
+        mbar_init(bar_fin, 3);       // the three issuing warps
         mbar_init(bar_apost, kTcBuilders);
         mbar_init(&bar_post[0], 1);
         mbar_init(&bar_post[1], 1);
@@ -1163,10 +1166,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const int gg = g_base + g;
                     const bool job_first = m.st == 0, job_last = m.st == prm.nst - 1;
                     const int slot_rem = slot_len - 1 - o;  // stages after this one in its slot
-                    if (o == 0 && re_side) {
+                    if (o == 0 && !im_side) {
+                        // the slot's pre-product operand (pre side) and post-product operand (Re side)
                         if (!(ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs))) break;
                         tc_fence_after();
-                        if (!(ok = premma())) break;
+                        if (pre_side && !(ok = premma())) break;
                     }
                     const int bb = gg % kTcBStages, use = gg / kTcBStages;  // B buffer and its use count
                     if (!(ok = mbar_wait_bounded(&bar_bready[bb], use & 1, kWaitNs))) break;
@@ -1178,7 +1182,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     tc_fence_after();
                     // X of the next pair ahead of this stage's main MMAs: the builders drained the
                     // TMEM buffer at this (first) stage of the current pair
-                    if (re_side && (o & 1) == 0 && slot_rem >= 2 && !(ok = premma())) break;
+                    if (pre_side) {
+                        if ((o & 1) == 0 && slot_rem >= 2 && !(ok = premma())) break;
+                        if (job_last && slot_rem == 0) mma_commit(bar_slotfree);  // its pre-products of the slot
+                        continue;
+                    }
                     const uint64_t r_start = (uint64_t)(nw - 1 - m.st + GG::DA_TE - 1);
                     const uint64_t are_h = ta[0] + r_start, are_l = ta[1] + r_start;
                     const uint64_t aim_h = ta[2] + r_start, aim_l = ta[3] + r_start;
@@ -1204,7 +1212,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         mma_ss(dim, are_l, bim_h, idesc, 1u);
                     }
                     mma_commit(&bar_mma[bb]);
-                    if (job_last && !re_side) {
+                    if (job_last && im_side) {
                         mma_commit(bar_job);
                         if (slot_rem == 0) mma_commit(bar_slotfree);
                     }
