@@ -1116,7 +1116,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         };
 
         if (ctl) {
-            // ================= MMA-issuing warps (lane 0): Re side and Im side =================
+            // ========== MMA-issuing warps (lane 0): Re side, Im side, pre-product side ==========
             if (lane == 0) {
                 // descriptors: fixed parts built once; a shift of the start address is an add
                 // on the descriptor's low field (shared addresses stay below 2^18)
