@@ -161,15 +161,21 @@ KERNEL_SOURCES = {
 
 # --- our arm ---------------------------------------------------------------------------
 
-def dist_setup(args):
+def dist_setup(args=None):
+    """Rank, world size and local rank from the launcher's environment; for N > 1 one
+    process group over NCCL (one rank per GPU), or gloo where there is no GPU (the host-side
+    logic is tested that way on CPU)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return world, rank, local
@@ -186,9 +192,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(points_per_rank_step, steps, world, max_total_ms):
+    """Points/s of the whole job: every rank runs its own replica of the workload, so the
+    job evaluates world x points per step, timed by the slowest rank."""
+    return points_per_rank_step * steps * world / (max_total_ms / 1e3)
 
 
 def time_steps(step, steps, warmup, world, stream, clocks=None, before_timed=None):
@@ -278,7 +291,7 @@ def run_ours(args):
     sse.sse_plan_set_timing(plan.handle, False)
     plan.status()
     total_ms_max = max_over_ranks(total_ms, world)
-    value = points * args.steps * world / (total_ms_max / 1e3)
+    value = whole_job_value(points, args.steps, world, total_ms_max)
     # our kernels per step: the workspace pass (re-encoded G and slot tables, per sign) of
     # the Nkz = 5 tensor-core form, then the main kernel
     launches_per_step = 1 + (4 if (form == "mixed" and info.kernel_id == 1 and geo.nkz == 5) else 0)
