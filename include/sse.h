@@ -107,8 +107,11 @@ typedef struct {
 /* Validate the geometry (copies neigh to the host once to range-check it: every entry
  * in [-1, na)), choose the kernel and its tiles, and allocate the plan.  On success
  * *out owns a plan that the caller frees with sse_plan_destroy.  A mixed-mode plan with
- * nkz = 5 also owns a workspace of 2 (ne na + 1) x 8 KB (G re-encoded for the tensor-core
- * product dH_i G, one half per sign), so executions of one plan must not overlap on the GPU:
+ * nkz = 5 and nw <= 50 (the warp-specialised tensor-core form) also owns a workspace of
+ * 2 (ne na + 1) x 8 KB (G re-encoded for the tensor-core product dH_i G) plus
+ * 2 na nb x (2 KB (nw + 14) + 26 KB) (each bond's operand tables), one half per sign:
+ * 2.6 GB for nkz = 5, ne = 256, na = 512, nb = 4, nw = 32.  Its size is reported in
+ * sse_plan_info.workspace_bytes.  Executions of one plan must not overlap on the GPU:
  * issue them on one stream or order them with events.  The batched form and the server
  * keep to this on their own (a plan that appears twice in one batch falls back to the
  * form without workspace; a server round holds a plan once). */
