@@ -8,7 +8,17 @@ seed 1): every row of the hot path (stage inputs, the q/w-independent products, 
 Inputs (3.0 GB of G plus Dt) are larger than the 129 MB L2, so no flush is needed
 between steps.
 
+Beside the headline the default run measures, each with at least 20 timed repetitions
+(p50/p99) and its own clock record:
+  * the plain FP64 form on the same medium workload ("vs plain FP64");
+  * the precision form: Na = 2048 (G about 6 GB per sign), mixed, complex128;
+  * the batched form: 64 uneven instances (Na ~ U[64,1024], NE ~ U[64,512], Nkz=Nqz=3,
+    Nw=16, 3..8 random neighbours, complex64) in one persistent, graph-captured launch;
+  * the serving form: 2000 Poisson-arriving requests (the batched size distribution plus
+    5 % Na=2048/NE=256 requests) over device-resident sessions, 120 GB budget, p50/p99.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form mixed|fp64] [--impl ours|reference]
+                  [--no-precision] [--no-batched] [--serving N]
 
 Prints ONE JSON line on rank 0.  Under torchrun each rank evaluates its own replica of
 the workload (replicas only: the single-instance path has no cross-GPU exchange), and
@@ -52,10 +62,14 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="timed steps of the plain FP64 form measured beside the mixed form")
-    ap.add_argument("--batched", action="store_true",
-                    help="also time the batched workload (64 uneven instances, one persistent launch)")
-    ap.add_argument("--serving", type=int, default=0, metavar="N",
-                    help="also run the serving workload with N Poisson-arriving requests (0: off)")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision leg (Na = 2048, mixed, complex128)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched leg (64 uneven instances, one persistent launch)")
+    ap.add_argument("--serving", type=int, default=2000, metavar="N",
+                    help="requests of the serving leg (Poisson arrivals; 0: skip the leg)")
+    ap.add_argument("--leg-steps", type=int, default=20,
+                    help="timed repetitions of each leg (p50/p99 need at least 20)")
     return ap.parse_args()
 
 
@@ -242,6 +256,56 @@ def pct(xs, p):
     return xs[i]
 
 
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def tensor_peak(peaks, clk):
+    """bf16 dense peak for a tensor-bound kernel, divided by the split products.  The burst
+    figure applies when the clock record of the timed region shows the SM clock at its
+    maximum and no power cap; otherwise the sustained (power-capped) figure."""
+    burst = peaks.get("bf16_tflops")
+    sustained = peaks.get("bf16_tflops_sustained")
+    src = "measured" if burst else "fallback"
+    burst = burst or 1900.0
+    sustained = sustained or 1700.0
+    full = (isinstance(clk, dict) and "sm_mhz" in clk and clk["sm_mhz"] >= 0.97 * clk["sm_max_mhz"]
+            and "sw_power_cap" not in clk.get("reasons", []))
+    bf16, kind = (burst, "burst") if full else (sustained, "sustained")
+    return bf16 / SPLIT_PRODUCTS, f"{src} bf16 {kind} {bf16} TFLOP/s / {SPLIT_PRODUCTS} split products"
+
+
+def leg_timing(step, steps, warmup, stream, uuid):
+    """W untimed steps, then `steps` steps each bracketed by CUDA events on `stream`, with
+    nvidia-smi sampling the clocks meanwhile.  Returns per-step ms and the clock record."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    return [e0.elapsed_time(e1) for e0, e1 in evs], clk
+
+
+def device_uuid():
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -279,11 +343,7 @@ def run_ours(args):
     def step():
         plan.execute(dev["G_gt"], dev["G_lt"], dev["D_gt"], dev["D_lt"], S["gt"], S["lt"], stream=stream)
 
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
-    except Exception:
-        pass
+    uuid = device_uuid()
     clocks = ClockSampler(uuid)
     total_ms, per_step, clk = time_steps(step, args.steps, args.warmup, world, stream, clocks,
                                          before_timed=lambda: sse.sse_plan_set_timing(plan.handle, True))
@@ -294,25 +354,20 @@ def run_ours(args):
     value = whole_job_value(points, args.steps, world, total_ms_max)
     # our kernels per step: the workspace pass (re-encoded G and slot tables, per sign) of
     # the Nkz = 5 tensor-core form, then the main kernel
-    launches_per_step = 1 + (4 if (form == "mixed" and info.kernel_id == 1 and geo.nkz == 5) else 0)
+    launches_per_step = 1 + (4 if (form == "mixed" and info.workspace_bytes > 1024) else 0)
     kern_ms = main_ms / timed_calls if timed_calls else statistics.mean(per_step)
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = load_peaks()
     tag, srcs = KERNEL_SOURCES[form]
     digest = source_digest(srcs)
     traffic = profiled_traffic(tag, digest)
     if form == "mixed":
-        bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
-        peak = bf16 / SPLIT_PRODUCTS
-        roof = {"bound": "tensor", "unit": "TFLOP/s",
-                "peak_source": f"measured bf16 sustained {bf16} TFLOP/s / {SPLIT_PRODUCTS} split products"}
+        peak, peak_src = tensor_peak(peaks, clk)
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": peak_src}
     else:
         peak = FP64_NOMINAL_TFLOPS
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (DFMA pipe)"}
+        roof = {"bound": "alu", "unit": "TFLOP/s",
+                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (DFMA pipe; no measured FP64 peak is recorded)"}
     achieved = flops_step / (kern_ms / 1e3) / 1e12
     roof.update({"kernel": tag, "kernel_ms": kern_ms,
                  "workspace_pass_ms": (prep_ms / timed_calls) if timed_calls else None,
@@ -336,12 +391,15 @@ def run_ours(args):
         def step64():
             p64.execute(dev["G_gt"], dev["G_lt"], dev["D_gt"], dev["D_lt"], S["gt"], S["lt"], stream=stream)
 
-        t64, ps64, _ = time_steps(step64, args.fp64_steps, 3, world, stream)
+        t64, ps64, clk64 = time_steps(step64, args.fp64_steps, 1, world, stream, ClockSampler(uuid))
         t64 = max_over_ranks(t64, world)
         v64 = points * args.fp64_steps * world / (t64 / 1e3)
         a64 = flops_step / (statistics.mean(ps64) / 1e3) / 1e12
         out["fp64_form"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
-                            "roofline_frac": a64 / FP64_NOMINAL_TFLOPS, "speedup_of_value": value / v64}
+                            "steps": args.fp64_steps, "roofline_frac": a64 / FP64_NOMINAL_TFLOPS,
+                            "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (not measured)",
+                            "speedup_of_value": value / v64, "clocks": clk64}
+        out["gpu_launches"] += args.fp64_steps + 1
         p64.close()
 
     hostin, hostout = {}, {}
@@ -365,19 +423,23 @@ def run_ours(args):
         out["e2e"] = {"value": points * k_e2e * world / e2e_s, "unit": UNIT, "steps": k_e2e,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "api": "sse_execute_host (pinned host buffers)"}
-        out["gpu_launches"] += k_e2e * launches_per_step + 1
+        out["gpu_launches"] += (k_e2e + 1) * launches_per_step
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_sample(inst, geo)
-    del hostin, hostout
-    if args.batched or args.serving:
-        del dev, S, plan_keep[:]
-        torch.cuda.empty_cache()
-    if args.batched:
-        out["batched"] = run_batched(args, stream, peaks)
+    del hostin, hostout, dev, S, inst
+    plan_keep.clear()
+    plan = None
+    torch.cuda.empty_cache()
+    if not args.no_precision and form == "mixed":
+        out["precision"] = run_precision(args, stream, peaks, uuid)
+        out["gpu_launches"] += out["precision"]["gpu_launches"]
+    if not args.no_batched and form == "mixed":
+        out["batched"] = run_batched(args, stream, peaks, uuid)
         out["gpu_launches"] += out["batched"]["gpu_launches"]
-    if args.serving:
-        out["serving"] = run_serving(args.serving)
+    if args.serving and form == "mixed":
+        out["serving"] = run_serving(args.serving, uuid)
+        out["gpu_launches"] += out["serving"]["gpu_launches"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -385,7 +447,48 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batched(args, stream, peaks):
+def run_precision(args, stream, peaks, uuid):
+    """The precision workload: Nkz=Nqz=5, NE=256, Nw=32, Na=2048, Nb=4 chain neighbours,
+    complex128 (G about 6 GB per sign), mixed form; inputs drawn on the device (seed 2).
+    Its error against the oracle on the Na=128 slice is checked by the parity tests."""
+    import torch
+
+    from paper_1912_08810_gb300 import inputs, sse
+    geo = inputs.PRECISION
+    inst = inputs.make_instance_torch(geo, 2, dtype=torch.complex128)
+    S = {s: torch.empty_like(inst["G_gt"]) for s in ("gt", "lt")}
+    plan = sse.Plan(inst["neigh"], inst["dH"], nkz=geo.nkz, nqz=geo.nqz, ne=geo.ne, nw=geo.nw, mode="mixed")
+    info = plan.info()
+    flops = 2 * info.flops_per_sign
+
+    def step():
+        plan.execute(inst["G_gt"], inst["G_lt"], inst["D_gt"], inst["D_lt"], S["gt"], S["lt"], stream=stream)
+
+    steps, warm = max(20, args.leg_steps), 3
+    sse.sse_plan_set_timing(plan.handle, True)
+    per, clk = leg_timing(step, steps, warm, stream, uuid)
+    prep_ms, main_ms, calls = sse.sse_plan_timing(plan.handle)
+    plan.status()
+    ms = statistics.mean(per)
+    kern_ms = main_ms / calls
+    peak, peak_src = tensor_peak(peaks, clk)
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    res = {"workload": "precision SSE: Nkz=Nqz=5, NE=256, Nw=32, Na=2048, Nb=4 chain, Norb=12, complex128, "
+                       "seed 2 (drawn on device)",
+           "points_per_step": geo.points(), "value": geo.points() / (ms / 1e3), "unit": UNIT,
+           "ms_per_step": ms, "p50_ms": pct(per, 50), "p99_ms": pct(per, 99), "steps": steps, "warmup": warm,
+           "gpu_launches": 5 * (steps + warm), "clocks": clk,
+           "roofline": {"bound": "tensor", "kernel": "sse_tc_kernel", "kernel_ms": kern_ms,
+                        "workspace_pass_ms": prep_ms / calls, "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_src,
+                        "algorithmic_flops_per_launch": flops}}
+    plan.close()
+    del inst, S
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batched(args, stream, peaks, uuid):
     """The batched workload: 64 instances (Na ~ U[64,1024], NE ~ U[64,512], Nkz=Nqz=3,
     Nw=16, 3..8 random neighbours within +-8 sites, complex64, seed 3), drawn on the device,
     evaluated by one persistent launch per step; the step is captured in a CUDA graph and
@@ -418,30 +521,21 @@ def run_batched(args, stream, peaks):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=side):
         sse.sse_execute_batch(handles, ios, side.cuda_stream)
-    steps, warm = max(2, min(args.steps, 3)), 1
-    for _ in range(warm):
-        graph.replay()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    steps, warm = max(20, args.leg_steps), 3
     cur = torch.cuda.current_stream()
-    for a, b in evs:
-        a.record(cur)
-        graph.replay()
-        b.record(cur)
-    torch.cuda.synchronize()
-    per = [a.elapsed_time(b) for a, b in evs]
+    per, clk = leg_timing(graph.replay, steps, warm, cur, uuid)
     plans[0].status()
     ms = statistics.mean(per)
-    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    peak, peak_src = tensor_peak(peaks, clk)
     achieved = flops / (ms / 1e3) / 1e12
     res = {"workload": "64 instances, Na~U[64,1024], NE~U[64,512], Nkz=Nqz=3, Nw=16, Nb~U{3..8} "
                        "within +-8 sites, complex64, seed 3 (drawn on device)",
            "points_per_step": points, "value": points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
            "p50_ms": pct(per, 50), "p99_ms": pct(per, 99), "steps": steps, "warmup": warm,
            "tiles_per_unit": tuning[0] if tuning else None, "longest_first": tuning[1] if tuning else None,
-           "autotune_s": tune_s, "graph_captured": True, "gpu_launches": steps + warm,
-           "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16 / SPLIT_PRODUCTS,
-                        "unit": "TFLOP/s", "frac": achieved / (bf16 / SPLIT_PRODUCTS)}}
+           "autotune_s": tune_s, "graph_captured": True, "gpu_launches": steps + warm + 12, "clocks": clk,
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "peak_source": peak_src,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "algorithmic_flops_per_launch": flops}}
     for p in plans:
         p.close()
     del insts, outs, graph
@@ -449,7 +543,7 @@ def run_batched(args, stream, peaks):
     return res
 
 
-def run_serving(n_requests, seed=4):
+def run_serving(n_requests, uuid, seed=4):
     """Serving workload: n_requests arriving as a Poisson stream over resident sessions
     drawn from the batched size distribution (95 %) plus large sessions (5 %: Na=2048,
     NE=256), each session an SCBA-style repeat (one request in flight per session, its
@@ -502,7 +596,9 @@ def run_serving(n_requests, seed=4):
     server = sse.sse_server_create(120 << 30, 64, 30000)
     busy = {}
     waiting = {i: [] for i in range(len(objs))}
-    lat, done_points = [], 0
+    lat, done_points, sizes = [], 0, []
+    clocks = ClockSampler(uuid)
+    clocks.start()
     t0 = time.perf_counter()
     nxt = 0
     inflight = {}
@@ -528,19 +624,24 @@ def run_serving(n_requests, seed=4):
                 sidx, rid, arr = inflight.pop(tk)
                 del busy[sidx]
                 lat.append((time.perf_counter() - t0 - arr) * 1e3)
+                sizes.append(r.round_size)
                 done_points += objs[sidx]["points"]
             time.sleep(0.0002)
         wall = time.perf_counter() - t0
         rounds, _, _ = sse.sse_server_stats(server)
     finally:
         sse.sse_server_destroy(server)
+    clk = clocks.stop()
     for o in objs:
         o["plan"].close()
     torch.cuda.empty_cache()
     return {"requests": n_requests, "sessions": len(objs), "large_fraction": 0.05,
             "arrival_rate_per_s": rate, "budget_gb": 120, "value": done_points / wall, "unit": UNIT,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(np.mean(lat)),
-            "rounds": rounds, "requests_per_round": n_requests / max(rounds, 1), "wall_s": wall}
+            "rounds": rounds, "requests_per_round": n_requests / max(rounds, 1),
+            "mean_round_size_seen": float(np.mean(sizes)), "wall_s": wall, "clocks": clk,
+            "gpu_launches": int(rounds) + 2 * len(objs),
+            "latency": "completion minus Poisson arrival time, host clock"}
 
 
 def cpu_sample(inst, geo, n_atoms=None):

@@ -72,7 +72,8 @@ typedef enum { SSE_C128 = 0, SSE_C64 = 1 } sse_dtype;
 
 /* SSE_MODE_FP64: every product and sum in FP64 (the oracle-matching reference form).
  * SSE_MODE_MIXED: products on the tensor cores from split-bf16 operands with FP32
- * accumulation, partial sums reduced into Sigma in FP64. */
+ * accumulation; the sum over neighbour slots into Sigma is FP64 for SSE_C128 and kept in
+ * the output's own FP32 for SSE_C64. */
 typedef enum { SSE_MODE_FP64 = 0, SSE_MODE_MIXED = 1 } sse_mode;
 
 typedef struct {
@@ -128,7 +129,7 @@ SSE_API sse_status sse_execute(sse_plan_t *plan, const sse_io *io, void *stream)
  * the stream before returning.  Staging is allocated on first use and kept. */
 SSE_API sse_status sse_execute_host(sse_plan_t *plan, const sse_io *host_io, void *stream);
 
-/* Batched form (row a6): evaluate n independent instances -- each with its own plan and
+/* Batched form: evaluate n independent instances -- each with its own plan and
  * buffers, uneven na, ne, nb_max and nqz allowed -- in one persistent launch of the
  * mixed kernel: one CTA per SM pulls work units (sign, atom, range of energy tiles) from
  * a device counter until none are left.  All plans must be SSE_MODE_MIXED with equal
@@ -139,8 +140,8 @@ SSE_API sse_status sse_execute_host(sse_plan_t *plan, const sse_io *host_io, voi
  * file named by SSE_AUTOTUNE_CACHE (SSE_AUTOTUNE=0 skips tuning).  After tuning, the call
  * is asynchronous and stream-ordered (it allocates its 4-byte work counter with
  * cudaMallocAsync on `stream`), so it can be captured in a CUDA graph.  Results equal those
- * of sse_execute on each instance alone, bit for bit.  Device-wait timeouts are recorded
- * in plans[0]'s status word. */
+ * of sse_execute on each instance alone, bit for bit.  Device-wait timeouts of every
+ * instance are recorded in plans[0]'s status word (read it with sse_plan_status(plans[0])). */
 SSE_API sse_status sse_execute_batch(sse_plan_t *const *plans, const sse_io *ios, int32_t n, void *stream);
 
 /* The autotuner's choice for this batch shape: SSE_OK with the values, or SSE_NOT_READY
@@ -148,38 +149,50 @@ SSE_API sse_status sse_execute_batch(sse_plan_t *const *plans, const sse_io *ios
 SSE_API sse_status sse_batch_tuning(sse_plan_t *const *plans, const sse_io *ios, int32_t n, int32_t *tiles_per_unit,
                                     int32_t *longest_first);
 
-/* ---- serving (row a7): a request loop with continuous batching -------------------------
+/* ---- serving: a request loop with continuous batching ------------------------------------
  *
- * A server owns a host thread and two CUDA streams on the device current at creation.
+ * A server owns a host thread and two CUDA streams on the device current at creation, each
+ * with its own device status word and work counter (allocated once, at creation).
  * Requests (a mixed-mode plan plus device buffers the caller keeps resident between SCBA
- * iterations) are admitted in arrival order while the sum of the admitted requests'
- * resident bytes (G, Dt and Sigma of each requested sign) stays within mem_budget_bytes
- * and at most max_inflight are admitted.  Every admitted request that has not started
- * joins the next round: one persistent batched launch (as sse_execute_batch, with the
- * tuned split when the shape was tuned before, else the default split), launched on the
- * stream the previous round did not use, so new arrivals start while older rounds drain.
- * A ticket borrows its plan and buffers until sse_poll returns a final status. */
+ * iterations) are admitted in arrival order while the admitted working set stays within
+ * mem_budget_bytes and at most max_inflight requests are admitted.  The working set counts
+ * each admitted request's resident bytes (G, Dt and Sigma of each requested sign) plus,
+ * once per plan held by an admitted request, the device memory that plan owns (its status
+ * word and tensor-core workspace).  Every admitted request that has not started joins the
+ * next round: one persistent batched launch (as sse_execute_batch, with the tuned split
+ * when the shape was tuned before, else the default split) on a stream that no running
+ * round uses, so new arrivals start while older rounds drain.  A round's device-wait
+ * timeouts are recorded in that round's own status word and reported on every ticket of
+ * the round.  A ticket borrows its plan and buffers until sse_poll returns a final status. */
 typedef struct {
     sse_status status;    /* final status once sse_poll stops returning SSE_NOT_READY */
     double t_submit_ms;   /* host steady-clock times (milliseconds) */
     double t_start_ms;    /* when its round was launched (0 while pending) */
-    double t_end_ms;      /* when the server saw its round complete */
+    double t_end_ms;      /* when the server saw its round complete (or cancelled it) */
     int32_t round_size;   /* requests in the round it ran in */
 } sse_result;
 
-/* wait_limit_ms bounds how long sse_server_destroy waits for running rounds (0: 1000). */
+/* wait_limit_ms bounds how long sse_server_shutdown / sse_server_destroy wait for running
+ * rounds (0: 1000). */
 SSE_API sse_status sse_server_create(uint64_t mem_budget_bytes, int32_t max_inflight, uint32_t wait_limit_ms,
                                      sse_server_t **out);
-/* Non-blocking.  SSE_E_OVER_BUDGET if the request alone exceeds the budget (it could never
- * be admitted); SSE_E_SHUTDOWN during destruction. */
+/* Non-blocking.  Precondition: every write to the request's input buffers (G, Dt) is
+ * complete on the device before the call -- the server's streams do not wait for the
+ * caller's streams (synchronise the stream that filled them, or wait on its event first).
+ * SSE_E_OVER_BUDGET if the request and its plan's workspace alone exceed the budget (it
+ * could never be admitted); SSE_E_SHUTDOWN after shutdown began. */
 SSE_API sse_status sse_submit(sse_server_t *server, sse_plan_t *plan, const sse_io *io, uint64_t *ticket);
 /* SSE_NOT_READY while queued or running; then the request's final status (SSE_OK, a CUDA
- * or timeout error, or SSE_E_CANCELLED), after which the ticket is forgotten and later
- * polls give SSE_E_UNKNOWN_TICKET.  `out` (may be NULL) receives status and timestamps. */
+ * error, SSE_E_TIMEOUT if a device wait of its round expired, SSE_E_OUT_OF_MEMORY, or
+ * SSE_E_CANCELLED), after which the ticket is forgotten and later polls give
+ * SSE_E_UNKNOWN_TICKET.  `out` (may be NULL) receives status and timestamps. */
 SSE_API sse_status sse_poll(sse_server_t *server, uint64_t ticket, sse_result *out);
-/* Cancels requests that have not started, waits up to wait_limit_ms for running rounds,
- * then frees the server (SSE_E_TIMEOUT, and the server is not freed, if rounds are still
- * running then). */
+/* Stops admitting, cancels every request that has not started (they end with
+ * SSE_E_CANCELLED and stay pollable) and waits up to wait_limit_ms for running rounds:
+ * SSE_OK once none runs, SSE_E_TIMEOUT otherwise.  Later submits give SSE_E_SHUTDOWN. */
+SSE_API sse_status sse_server_shutdown(sse_server_t *server);
+/* sse_server_shutdown, then frees the server (SSE_E_TIMEOUT, and the server is not freed,
+ * if rounds are still running after wait_limit_ms). */
 SSE_API sse_status sse_server_destroy(sse_server_t *server);
 /* Rounds launched so far and the admitted working set (bytes, requests). */
 SSE_API sse_status sse_server_stats(sse_server_t *server, uint64_t *rounds, uint64_t *inflight_bytes,
@@ -212,9 +225,25 @@ SSE_API sse_status sse_plan_timing(sse_plan_t *plan, double *prep_ms, double *ma
  * calls whose work overlaps on the GPU race.  Same arguments and results as sse_plan +
  * sse_execute in SSE_MODE_MIXED; geometries the mixed kernel cannot run (Nkz > 5,
  * nb_max > 32, or a shared-memory need beyond one SM) are rejected with
- * SSE_E_INVALID_ARG.  Synchronous: returns after Sigma is written (it synchronises
- * `stream`); SSE_E_TIMEOUT if a bounded device wait expired. */
+ * SSE_E_INVALID_ARG.  Every call synchronises `stream` twice (after the on-device
+ * neighbour check, whose result it reads back, and at the end) and so blocks the calling
+ * thread until Sigma is written; SSE_E_TIMEOUT if a bounded device wait expired. */
 SSE_API sse_status sse_execute_noalloc(const sse_geometry *geo, const sse_io *io, void *stream);
+
+/* Failure injection for tests of the failure detection; the paper has no counterpart.
+ * Arms a one-shot, process-wide fault that the next matching event consumes:
+ *   SSE_INJECT_STALL: the next launch of a mixed-mode kernel (sse_execute, sse_execute_batch
+ *     or a server round) leaves one wait of each work unit's pipeline unsatisfied (the
+ *     warp-specialised form skips the copy of a neighbour slot's operand tables; the other
+ *     form skips the copy of one stage's G blocks).  The bounded device wait expires, the
+ *     kernel drains what it has in flight, frees its tensor memory and returns; its status
+ *     word reads SSE_E_TIMEOUT (sse_plan_status, sse_poll), Sigma is undefined, and the
+ *     context stays usable.  Costs a few bounded waits of 0.25 s.
+ *   SSE_INJECT_ALLOC_FAIL: the next per-request device allocation (a plan's workspace, the
+ *     work counter of a batched launch) reports SSE_E_OUT_OF_MEMORY without allocating.
+ *   SSE_INJECT_NONE: disarm. */
+enum { SSE_INJECT_NONE = 0, SSE_INJECT_STALL = 1, SSE_INJECT_ALLOC_FAIL = 2 };
+SSE_API sse_status sse_debug_inject(int32_t kind);
 
 SSE_API const char *sse_status_string(sse_status status);
 SSE_API const char *sse_last_error(void);

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -14,6 +15,12 @@
 namespace sse {
 
 static thread_local std::string t_error;
+static std::atomic<int32_t> g_inject{SSE_INJECT_NONE};
+
+bool take_inject(int32_t kind) {
+    int32_t expect = kind;
+    return kind != SSE_INJECT_NONE && g_inject.compare_exchange_strong(expect, SSE_INJECT_NONE);
+}
 
 void set_error(const char *fmt, ...) {
     char buf[512];
@@ -335,7 +342,7 @@ sse_status sse_execute_batch(sse_plan_t *const *plans, const sse_io *ios, int32_
         slots[i] = plans[i]->slots_per_atom;
         plans[i]->last_stream = (cudaStream_t)stream;
     }
-    return run_batch(ps.data(), slots.data(), ios, n, (cudaStream_t)stream, nullptr, nullptr);
+    return run_batch(ps.data(), slots.data(), ios, n, (cudaStream_t)stream, plans[0]->d_status, nullptr, nullptr);
 }
 
 sse_status sse_batch_tuning(sse_plan_t *const *plans, const sse_io *ios, int32_t n, int32_t *tiles_per_unit,
@@ -376,6 +383,13 @@ sse_status sse_plan_timing(sse_plan_t *plan, double *prep_ms, double *main_ms, i
     if (prep_ms) *prep_ms = t.prep_ms;
     if (main_ms) *main_ms = t.main_ms;
     if (calls) *calls = t.done;
+    return SSE_OK;
+}
+
+sse_status sse_debug_inject(int32_t kind) {
+    if (kind != SSE_INJECT_NONE && kind != SSE_INJECT_STALL && kind != SSE_INJECT_ALLOC_FAIL)
+        return set_error("unknown injection kind %d", kind), SSE_E_INVALID_ARG;
+    g_inject.store(kind);
     return SSE_OK;
 }
 

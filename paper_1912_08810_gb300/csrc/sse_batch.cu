@@ -105,7 +105,7 @@ std::vector<int> make_order(Plan *const *plans, const double *slots_per_atom, in
 }  // namespace
 
 sse_status run_batch(Plan *const *plans, const double *slots_per_atom, const sse_io *ios, int n, cudaStream_t st,
-                     int *tpc_out, int *lpt_out, bool allow_tune) {
+                     int32_t *status, int *tpc_out, int *lpt_out, bool allow_tune, int32_t *queue_in) {
     if (n == 0) return SSE_OK;
     const unsigned long long sig = signature(plans, ios, n);
     Choice ch{2, 1};
@@ -119,9 +119,13 @@ sse_status run_batch(Plan *const *plans, const double *slots_per_atom, const sse
             have = true;
         }
     }
-    int32_t *queue = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&queue, sizeof(int32_t), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(work counter)");
+    int32_t *queue = queue_in;
+    cudaError_t e = cudaSuccess;
+    if (!queue) {
+        if (take_inject(SSE_INJECT_ALLOC_FAIL)) return set_error("injected allocation failure (work counter)"), SSE_E_OUT_OF_MEMORY;
+        e = cudaMallocAsync((void **)&queue, sizeof(int32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(work counter)");
+    }
     sse_status rs = SSE_OK;
     const char *tune_env = getenv("SSE_AUTOTUNE");
     if (!have && allow_tune && !(tune_env && tune_env[0] == '0')) {
@@ -151,13 +155,13 @@ sse_status run_batch(Plan *const *plans, const double *slots_per_atom, const sse
         const int tpcs[] = {1, 2, 4, 8, 16};
         {
             std::vector<int> order = make_order(sp.data(), ss.data(), m, 2, true);
-            rs = launch_mixed_batch(sp.data(), sio.data(), order.data(), m, 2, queue, st);
+            rs = launch_mixed_batch(sp.data(), sio.data(), order.data(), m, 2, queue, status, st);
         }
         for (int lpt = 0; lpt < 2 && rs == SSE_OK; ++lpt)
             for (int tpc : tpcs) {
                 std::vector<int> order = make_order(sp.data(), ss.data(), m, tpc, lpt != 0);
                 cudaEventRecord(e0, st);
-                rs = launch_mixed_batch(sp.data(), sio.data(), order.data(), m, tpc, queue, st);
+                rs = launch_mixed_batch(sp.data(), sio.data(), order.data(), m, tpc, queue, status, st);
                 if (rs != SSE_OK) break;
                 cudaEventRecord(e1, st);
                 e = cudaEventSynchronize(e1);
@@ -182,9 +186,9 @@ sse_status run_batch(Plan *const *plans, const double *slots_per_atom, const sse
     }
     if (rs == SSE_OK) {
         std::vector<int> order = make_order(plans, slots_per_atom, n, ch.tpc, ch.lpt != 0);
-        rs = launch_mixed_batch(plans, ios, order.data(), n, ch.tpc, queue, st);
+        rs = launch_mixed_batch(plans, ios, order.data(), n, ch.tpc, queue, status, st);
     }
-    cudaFreeAsync(queue, st);
+    if (!queue_in) cudaFreeAsync(queue, st);
     if (tpc_out) *tpc_out = ch.tpc;
     if (lpt_out) *lpt_out = ch.lpt;
     return rs;

@@ -72,14 +72,20 @@ double algorithmic_cmacs(const Dims &d, const std::vector<int32_t> &neigh_host);
 sse_status launch_fp64_direct(const Plan &p, const sse_io &io, cudaStream_t st);
 sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st);
 // Persistent launch over n instances in the given order (all plans mixed, with equal
-// nkz, nw, omega_first and dtype), `tpc` tiles per work unit, `queue` a device counter.
+// nkz, nw, omega_first and dtype), `tpc` tiles per work unit, `queue` a device counter;
+// expired device waits are recorded in the device word `status`.
 sse_status launch_mixed_batch(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
-                              int32_t *queue, cudaStream_t st);
+                              int32_t *queue, int32_t *status, cudaStream_t st);
 // Batched execution with the autotuned work split (sse_batch.cu); slots_per_atom[i] is the
-// mean number of valid neighbour slots of plans[i].
-// Without allow_tune an untuned shape runs with the default split instead of tuning.
+// mean number of valid neighbour slots of plans[i]; `status` receives expired device waits.
+// Without allow_tune an untuned shape runs with the default split instead of tuning.  With
+// `queue` (a device int32 owned by the caller) no work counter is allocated.
 sse_status run_batch(Plan *const *plans, const double *slots_per_atom, const sse_io *ios, int n, cudaStream_t st,
-                     int *tpc_out, int *lpt_out, bool allow_tune = true);
+                     int32_t *status, int *tpc_out, int *lpt_out, bool allow_tune = true, int32_t *queue = nullptr);
+
+// One-shot test hooks (sse_debug_inject): take_inject(kind) returns true once after the
+// hook was armed with that kind.
+bool take_inject(int32_t kind);
 bool batch_choice(Plan *const *plans, const sse_io *ios, int n, int *tpc, int *lpt);
 sse_status mixed_plan_init(Plan &p);
 void mixed_plan_free(Plan &p);

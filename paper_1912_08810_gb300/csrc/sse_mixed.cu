@@ -96,6 +96,7 @@ struct MixParams {
     int32_t nkz, nw, omega_first;
     int32_t nst;            // stages per job
     int32_t n_inst;
+    int32_t inject;         // failure-injection test hook (sse_debug_inject): skip one copy per CTA
     long long total_units;
     uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, off_x, off_bp, g_stage;
     InstDesc inst[kMaxInst];
@@ -188,16 +189,19 @@ __device__ __forceinline__ float2 slot_sum<float2>(float2 v, float2 old, bool fi
     return make_float2(f64_to_f32(x), f64_to_f32(y));
 }
 
-// Running sum over neighbour slots kept in FP32 in the output element itself (its first 8
-// bytes) until the last slot, which writes the element in its own type.
-template <typename CT>
-__device__ __forceinline__ float2 *partial_of(CT *p) { return reinterpret_cast<float2 *>(p); }
+// Sum over neighbour slots in the warp-specialised form: the first slot's contribution is
+// stored in the output type; each later slot's FP32 contribution is added in place by a
+// reduction at L2 -- widened exactly and added in FP64 for complex128 output (the running
+// sum over slots is an FP64 sum), added in FP32 for complex64 output (the output's own
+// precision).
 template <typename CT>
 __device__ __forceinline__ CT final_of(float2 v);
 template <>
 __device__ __forceinline__ double2 final_of<double2>(float2 v) { return make_double2(f32_to_f64(v.x), f32_to_f64(v.y)); }
 template <>
 __device__ __forceinline__ float2 final_of<float2>(float2 v) { return v; }
+__device__ __forceinline__ void slot_add(double2 *p, float2 v) { red_add_f64x2(p, f32_to_f64(v.x), f32_to_f64(v.y)); }
+__device__ __forceinline__ void slot_add(float2 *p, float2 v) { red_add_f2(p, v); }
 
 template <int NK, typename CT>
 __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_constant__ MixParams prm) {
@@ -351,7 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         }
     };
     // Thread 0: bulk-copy the G blocks of stage g (at position q) into raw buffer g % 2.
+    // The failure-injection hook leaves the second stage of the CTA's first unit uncopied.
     auto issue_g = [&](int g, const Pos &q) {
+        if (prm.inject && iter == 0 && g == (total > 1 ? 1 : 0)) return;
         const int t = q.t, vs = q.vs, st = q.st;
         const int f = s_f[vs];
         const int e_first = t * GG::TE - omega_max + GG::P * st;
@@ -1286,13 +1292,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     // done (the CTA's first slot: nothing to wait for)
                     if (!(ok = mbar_wait_bounded(bar_slotfree, (slot_cp & 1) ^ 1, kWaitNs))) break;
                     // the small operands first: the pre-product can start while the table streams in
-                    const uint8_t *src = I.sws[sign] + ((size_t)a * d.nb + s_slot[vs]) * ebytes;
-                    mbar_arrive_expect_tx(bar_slot, 16384 + 2 * kPostBPlane);
-                    bulk_g2s(sApre, src + tbytes, 16384, bar_slot);
-                    bulk_g2s(sBpost, src + tbytes + 16384, 2 * kPostBPlane, bar_slot);
-                    mbar_arrive_expect_tx(bar_tab, tbytes);
-                    bulk_g2s(sTab, src, tbytes, bar_tab);
-                    ++slot_cp;
+                    // (the failure-injection hook skips the tables of the CTA's first unit's second
+                    // slot, its only slot if it has one)
+                    if (!(prm.inject && iter == 0 && vs == (nvalid > 1 ? 1 : 0))) {
+                        const uint8_t *src = I.sws[sign] + ((size_t)a * d.nb + s_slot[vs]) * ebytes;
+                        mbar_arrive_expect_tx(bar_slot, 16384 + 2 * kPostBPlane);
+                        bulk_g2s(sApre, src + tbytes, 16384, bar_slot);
+                        bulk_g2s(sBpost, src + tbytes + 16384, 2 * kPostBPlane, bar_slot);
+                        mbar_arrive_expect_tx(bar_tab, tbytes);
+                        bulk_g2s(sTab, src, tbytes, bar_tab);
+                        ++slot_cp;
+                    }
                     for (; pr < npairs && ok; ++pr) ok = issue_pair(2 * pr, f);
                 }
                 if (!ok) {
@@ -1416,7 +1426,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     ++job_ctr;
                     builders_sync();  // every builder is done with B before the A tile overlays it
                     tc_fence_after();
-                    const bool first_slot = vs == 0, last_slot = vs == nvalid - 1;
+                    const bool first_slot = vs == 0;
                     // A-tile role: warp -> (lane quarter, row r' of the tile); lane -> accumulator row
                     const int aq = warp & 3, arl = warp >> 2;
                     const int am = aq * 32 + lane;
@@ -1426,7 +1436,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const int drow = dq * 32 + lane;  // tile row (r', e, k)
                     const int drl = drow / 40, de = (drow / 5) % 8, dk = drow % 5;
                     const bool dlive = drow < 120 && E0 + de < d.ne;
-                    float2 old[4];
                     CT *dst = S;
                     // Tile q: its A is built once the MMAs of tile q - 1 are done (one A buffer);
                     // the accumulator columns it needs are loaded before that wait, and tile
@@ -1485,27 +1494,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tc_fence_before();
                         }
                         if (q > 0 && dlive) {
-                            // first slot: store; middle slots: add in place without waiting; last
-                            // slot: the sum so far (read one tile ahead) plus this one, in the output type
+                            // the slot's FP32 contribution into Sigma: the first slot stores it, every
+                            // later slot adds it with a fire-and-forget reduction at L2 (FP64 adds for
+                            // complex128, the running sum then being FP64; FP32 adds for complex64)
 #pragma unroll
                             for (int s2 = 0; s2 < 4; ++s2) {
                                 const float2 v = make_float2(pv[2 * s2], pv[2 * s2 + 1]);
-                                if (first_slot && last_slot) dst[s2] = final_of<CT>(v);
-                                else if (first_slot) *partial_of(dst + s2) = v;
-                                else if (!last_slot || sizeof(CT) == 8) red_add_f2(partial_of(dst + s2), v);
-                                else dst[s2] = final_of<CT>(make_float2(v.x + old[s2].x, v.y + old[s2].y));
+                                if (first_slot) dst[s2] = final_of<CT>(v);
+                                else slot_add(dst + s2, v);
                             }
                         }
-                        if (q < 4) {
-                            // the slots summed so far for the rows this thread takes from tile q
+                        if (q < 4)
                             dst = S + (((size_t)dk * d.ne + (dlive ? E0 + de : 0)) * d.na + a) * kCh + (3 * q + drl) * 12 +
                                   4 * dsub;
-#pragma unroll
-                            for (int s2 = 0; s2 < 4; ++s2) {
-                                old[s2] = make_float2(0.f, 0.f);
-                                if (dlive && !first_slot && last_slot && sizeof(CT) == 16) old[s2] = *partial_of(dst + s2);
-                            }
-                        }
                     }
                     tile_ctr += 4;
                 }
@@ -1715,6 +1716,7 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     while (tpc > 1 && per_chunk * ((ntiles + tpc - 1) / tpc) < 8LL * sms) tpc = (tpc + 1) / 2;
     if (!fill_inst<NK>(prm.inst[0], p, io, tpc)) return SSE_OK;
     prm.n_inst = 1;
+    prm.inject = take_inject(SSE_INJECT_STALL) ? 1 : 0;
     prm.inst[0].unit_begin = 0;
     prm.total_units = inst_units(prm.inst[0]);
     prm.queue = nullptr;
@@ -1740,13 +1742,13 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
 // Persistent launches over many instances: one CTA per SM pulls units from a counter.
 template <int NK, typename CT, bool V3>
 sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
-                           int32_t *queue, cudaStream_t st) {
+                           int32_t *queue, int32_t *status, cudaStream_t st) {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plans[0]->device);
     for (int base = 0; base < n; base += kMaxInst) {
         MixParams prm{};
         uint32_t smem = 0;
-        sse_status rs = prepare<NK, CT, V3>(prm, smem, plans[order[base]]->d, plans[order[base]]->d_status);
+        sse_status rs = prepare<NK, CT, V3>(prm, smem, plans[order[base]]->d, status);
         if (rs != SSE_OK) return rs;
         long long units = 0;
         int m = 0;
@@ -1765,6 +1767,7 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
         }
         if (m == 0) continue;
         prm.n_inst = m;
+        prm.inject = (base == 0 && take_inject(SSE_INJECT_STALL)) ? 1 : 0;
         prm.total_units = units;
         prm.queue = queue;
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
@@ -1796,12 +1799,12 @@ sse_status launch_dtype(Plan &p, const sse_io &io, cudaStream_t st) {
 
 template <typename CT>
 sse_status launch_batch_dtype(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
-                              int32_t *queue, cudaStream_t st) {
+                              int32_t *queue, int32_t *status, cudaStream_t st) {
     switch (plans[order[0]]->d.nkz) {
-        case 1: return launch_batch_nk<1, CT, false>(plans, ios, order, n, tpc, queue, st);
-        case 2: return launch_batch_nk<2, CT, false>(plans, ios, order, n, tpc, queue, st);
-        case 3: return launch_batch_nk<3, CT, false>(plans, ios, order, n, tpc, queue, st);
-        case 4: return launch_batch_nk<4, CT, false>(plans, ios, order, n, tpc, queue, st);
+        case 1: return launch_batch_nk<1, CT, false>(plans, ios, order, n, tpc, queue, status, st);
+        case 2: return launch_batch_nk<2, CT, false>(plans, ios, order, n, tpc, queue, status, st);
+        case 3: return launch_batch_nk<3, CT, false>(plans, ios, order, n, tpc, queue, status, st);
+        case 4: return launch_batch_nk<4, CT, false>(plans, ios, order, n, tpc, queue, status, st);
         case 5: {
             // the pre-product form needs each plan's workspace for itself: every plan once
             bool all_ws = true;
@@ -1809,8 +1812,8 @@ sse_status launch_batch_dtype(Plan *const *plans, const sse_io *ios, const int *
                 all_ws = plans[order[x]]->mixed_ws != nullptr;
                 for (int y = 0; y < x && all_ws; ++y) all_ws = plans[order[y]] != plans[order[x]];
             }
-            return all_ws ? launch_batch_nk<5, CT, true>(plans, ios, order, n, tpc, queue, st)
-                          : launch_batch_nk<5, CT, false>(plans, ios, order, n, tpc, queue, st);
+            return all_ws ? launch_batch_nk<5, CT, true>(plans, ios, order, n, tpc, queue, status, st)
+                          : launch_batch_nk<5, CT, false>(plans, ios, order, n, tpc, queue, status, st);
         }
         default:
             set_error("mixed mode supports Nkz <= 5");
@@ -1857,7 +1860,7 @@ sse_status mixed_plan_init(Plan &p) {
         const size_t sign_bytes = ((size_t)d.ne * d.na + 1) * 8192;
         const size_t tab_sign = (size_t)d.na * d.nb * tc_entry_bytes(d.nw);
         const size_t bytes = 2 * sign_bytes + 2 * tab_sign;
-        cudaError_t e = cudaMalloc(&p.mixed_ws, bytes);
+        cudaError_t e = take_inject(SSE_INJECT_ALLOC_FAIL) ? cudaErrorMemoryAllocation : cudaMalloc(&p.mixed_ws, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             p.mixed_ws = nullptr;
@@ -1886,10 +1889,10 @@ sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st) {
 }
 
 sse_status launch_mixed_batch(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
-                              int32_t *queue, cudaStream_t st) {
+                              int32_t *queue, int32_t *status, cudaStream_t st) {
     if (n <= 0) return SSE_OK;
-    if (plans[order[0]]->geo.dtype == SSE_C128) return launch_batch_dtype<double2>(plans, ios, order, n, tpc, queue, st);
-    return launch_batch_dtype<float2>(plans, ios, order, n, tpc, queue, st);
+    if (plans[order[0]]->geo.dtype == SSE_C128) return launch_batch_dtype<double2>(plans, ios, order, n, tpc, queue, status, st);
+    return launch_batch_dtype<float2>(plans, ios, order, n, tpc, queue, status, st);
 }
 
 }  // namespace sse

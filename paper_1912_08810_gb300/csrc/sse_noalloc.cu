@@ -15,7 +15,9 @@
 // cudaGetSymbolAddress (with that device current) and caches it; make that first call
 // before any stream capture.  All calls on a device share the array: the words a call
 // relies on starting at zero are cleared at the start of every call, and two calls whose
-// work overlaps on the GPU (other streams, other threads) race on it.
+// work overlaps on the GPU (other streams, other threads) race on it.  Every call reads
+// the neighbour check's result and the kernel's wait status back to the host, so it
+// synchronises its stream twice and blocks the calling thread until Sigma is written.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -3,10 +3,12 @@
 // device buffers that the caller keeps resident between iterations.  A server thread
 // admits pending requests in arrival order while the admitted working sets fit the memory
 // budget and the in-flight cap, and launches every admitted-but-not-started request as one
-// persistent batched round on one of two streams.  Rounds alternate streams, so a round
-// formed from new arrivals starts while the previous one is still draining: continuous
-// batching rather than one queue drained at a time.  Completion is detected with events;
-// sse_poll reports status and timestamps.
+// persistent batched round.  The server owns kSlots streams, each with its own device
+// status word and work counter; a round is launched on a stream that no running round
+// uses, so a round formed from new arrivals starts while older rounds drain: continuous
+// batching rather than one queue drained at a time.  Each round copies its status word to
+// pinned host memory behind its kernels and records an event; the server thread polls the
+// events and never synchronises a stream.  sse_poll reports status and timestamps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +27,8 @@ using namespace sse;
 
 namespace {
 
+constexpr int kSlots = 2;  // streams, and so rounds in flight at once
+
 double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
@@ -35,18 +39,26 @@ enum ReqState { kPending = 0, kAdmitted = 1, kRunning = 2, kDone = 3 };
 struct Request {
     sse_plan_t *plan = nullptr;
     sse_io io{};
-    uint64_t bytes = 0;
+    uint64_t bytes = 0;  // G, Dt and Sigma of the requested signs (the plan's workspace is counted per plan)
     double t_submit = 0, t_start = 0, t_end = 0;
     sse_status status = SSE_NOT_READY;
     ReqState state = kPending;
     int round_size = 0;
 };
 
-struct Round {
+// One stream with what a round on it needs: the device status word and work counter
+// (d_words[0], d_words[1]), the pinned host copy of the status word, the completion event.
+struct Slot {
+    cudaStream_t stream = nullptr;
+    int32_t *d_words = nullptr;
+    volatile int32_t *h_status = nullptr;
     cudaEvent_t done = nullptr;
-    int stream = 0;
+    bool busy = false;
+};
+
+struct Round {
+    int slot = 0;
     std::vector<uint64_t> tickets;
-    double t_launch = 0;
 };
 
 }  // namespace
@@ -55,7 +67,8 @@ struct sse_server_s {
     std::mutex mu;
     std::condition_variable cv;
     std::thread thread;
-    bool stop = false;
+    bool stop = false;        // shutdown requested: admit nothing more
+    bool thread_done = false;  // the server thread has left its loop
     int device = 0;
     uint64_t budget = 0, inflight_bytes = 0;
     int max_inflight = 1, inflight = 0;
@@ -63,9 +76,11 @@ struct sse_server_s {
     uint64_t next_ticket = 1;
     std::deque<uint64_t> pending;
     std::unordered_map<uint64_t, Request> reqs;
+    std::unordered_map<const sse_plan_t *, int> plan_refs;  // admitted requests per plan
     std::vector<Round> running;
-    cudaStream_t streams[2] = {nullptr, nullptr};
-    int next_stream = 0;
+    Slot slots[kSlots];
+    int32_t *d_words = nullptr;
+    int32_t *h_words = nullptr;
     uint64_t rounds_launched = 0;
 };
 
@@ -85,6 +100,35 @@ uint64_t request_bytes(const Plan &p, const sse_io &io) {
     return per_sign * ((io.S_gt != nullptr) + (io.S_lt != nullptr));
 }
 
+// Device bytes the library holds for a plan (status word and tensor-core workspace).
+uint64_t plan_bytes(const Plan &p) { return (uint64_t)p.workspace_bytes; }
+
+// Bytes admitting request q adds to the working set: its buffers, plus its plan's
+// workspace when no admitted request holds that plan yet.
+uint64_t admit_bytes(const sse_server_s *s, const Request &q) {
+    auto it = s->plan_refs.find(q.plan);
+    const bool held = it != s->plan_refs.end() && it->second > 0;
+    return q.bytes + (held ? 0 : plan_bytes(*plan_core(q.plan)));
+}
+
+void admit(sse_server_s *s, Request &q) {
+    s->inflight_bytes += admit_bytes(s, q);
+    s->plan_refs[q.plan] += 1;
+    s->inflight += 1;
+    q.state = kAdmitted;
+}
+
+// Undo admit() once the request is final.
+void release(sse_server_s *s, Request &q) {
+    s->inflight_bytes -= q.bytes;
+    auto it = s->plan_refs.find(q.plan);
+    if (it != s->plan_refs.end() && --it->second == 0) {
+        s->inflight_bytes -= plan_bytes(*plan_core(q.plan));
+        s->plan_refs.erase(it);
+    }
+    s->inflight -= 1;
+}
+
 // Two plans can share a persistent launch when the compile-time shape and the shared
 // launch parameters agree.
 bool compatible(const Plan &a, const Plan &b) {
@@ -101,41 +145,51 @@ void finish_round(sse_server_s *s, Round &r, sse_status st) {
         q.state = kDone;
         q.t_end = t;
         if (q.status == SSE_NOT_READY) q.status = st;
-        s->inflight_bytes -= q.bytes;
-        s->inflight -= 1;
+        release(s, q);
     }
-    if (r.done) cudaEventDestroy(r.done);
-    r.done = nullptr;
+    s->slots[r.slot].busy = false;
 }
 
-// Launch every admitted request of one compatible group as a round.  Called with the lock.
-void launch_round(sse_server_s *s, std::vector<uint64_t> &group) {
+// Launch the admitted requests in `group` as one round on a free slot.  Called with the
+// lock held; releases it around the CUDA calls (only this thread launches rounds, and
+// running requests are touched by nobody else).
+void launch_round(sse_server_s *s, std::unique_lock<std::mutex> &lock, std::vector<uint64_t> &group) {
+    int si = 0;
+    while (si < kSlots && s->slots[si].busy) ++si;
+    if (si == kSlots) return;  // the caller keeps at most kSlots rounds running
+    Slot &slot = s->slots[si];
+    slot.busy = true;
     Round r;
-    r.stream = s->next_stream;
-    s->next_stream ^= 1;
+    r.slot = si;
     r.tickets = group;
-    r.t_launch = now_ms();
+    const double t_launch = now_ms();
     std::vector<Plan *> plans;
-    std::vector<double> slots;
+    std::vector<double> slots_per_atom;
     std::vector<sse_io> ios;
     for (uint64_t tk : group) {
         Request &q = s->reqs[tk];
         q.state = kRunning;
-        q.t_start = r.t_launch;
+        q.t_start = t_launch;
         q.round_size = (int)group.size();
         plans.push_back(plan_core(q.plan));
-        slots.push_back(plan_slots_per_atom(q.plan));
+        slots_per_atom.push_back(plan_slots_per_atom(q.plan));
         ios.push_back(q.io);
     }
-    cudaStream_t st = s->streams[r.stream];
-    sse_status rs = run_batch(plans.data(), slots.data(), ios.data(), (int)plans.size(), st, nullptr, nullptr,
-                              /*allow_tune=*/false);
-    if (rs == SSE_OK) {
-        cudaError_t e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(r.done, st);
-        if (e != cudaSuccess) rs = cuda_fail(e, "record round event");
-    }
     s->rounds_launched += 1;
+    lock.unlock();
+    cudaStream_t st = slot.stream;
+    sse_status rs = SSE_OK;
+    cudaError_t e = cudaMemsetAsync(slot.d_words, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) rs = cuda_fail(e, "clear the round's status word");
+    if (rs == SSE_OK)
+        rs = run_batch(plans.data(), slots_per_atom.data(), ios.data(), (int)plans.size(), st, slot.d_words, nullptr,
+                       nullptr, /*allow_tune=*/false, slot.d_words + 1);
+    if (rs == SSE_OK) {
+        e = cudaMemcpyAsync((void *)slot.h_status, slot.d_words, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaEventRecord(slot.done, st);
+        if (e != cudaSuccess) rs = cuda_fail(e, "record the round's completion");
+    }
+    lock.lock();
     if (rs != SSE_OK) {
         finish_round(s, r, rs);
         return;
@@ -147,44 +201,33 @@ void server_loop(sse_server_s *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lock(s->mu);
     while (true) {
-        // completions
+        // completions: a round is done when its event has fired; its status word (copied to
+        // pinned host memory behind the kernels) then holds every expired device wait
         for (size_t i = 0; i < s->running.size();) {
-            cudaError_t e = cudaEventQuery(s->running[i].done);
+            Slot &slot = s->slots[s->running[i].slot];
+            cudaError_t e = cudaEventQuery(slot.done);
             if (e == cudaErrorNotReady) {
                 ++i;
                 continue;
             }
             sse_status st = SSE_OK;
             if (e != cudaSuccess) st = cuda_fail(e, "round");
-            // a device wait that expired is recorded in the first plan's status word
-            if (st == SSE_OK) {
-                Request &q0 = s->reqs[s->running[i].tickets[0]];
-                cudaStream_t rst = s->streams[s->running[i].stream];
-                int32_t v = 0;
-                if (cudaMemcpyAsync(&v, plan_core(q0.plan)->d_status, sizeof v, cudaMemcpyDeviceToHost, rst) ==
-                        cudaSuccess &&
-                    cudaStreamSynchronize(rst) == cudaSuccess && v != 0) {
-                    cudaMemsetAsync(plan_core(q0.plan)->d_status, 0, sizeof v, rst);
-                    st = SSE_E_TIMEOUT;
-                }
-            }
+            else if (*slot.h_status != 0) st = SSE_E_TIMEOUT;
             finish_round(s, s->running[i], st);
             s->running.erase(s->running.begin() + (long)i);
         }
         if (s->stop && s->running.empty()) break;
-        // admission in arrival order while the working sets fit
         if (!s->stop) {
+            // admission in arrival order while the working sets fit
             while (!s->pending.empty()) {
                 Request &q = s->reqs[s->pending.front()];
-                if (s->inflight >= s->max_inflight || s->inflight_bytes + q.bytes > s->budget) break;
-                q.state = kAdmitted;
-                s->inflight += 1;
-                s->inflight_bytes += q.bytes;
+                if (s->inflight >= s->max_inflight || s->inflight_bytes + admit_bytes(s, q) > s->budget) break;
+                admit(s, q);
                 s->pending.pop_front();
             }
-            // one round per compatible group of admitted requests, at most two rounds queued;
-            // a plan runs in one round at a time and once per round (its workspace is its own)
-            while (s->running.size() < 2) {
+            // one round per compatible group of admitted requests while a stream is free; a
+            // plan runs in one round at a time and once per round (its workspace is its own)
+            while ((int)s->running.size() < kSlots && !s->stop) {
                 std::vector<uint64_t> group;
                 std::vector<const sse_plan_t *> busy;
                 for (const Round &r : s->running)
@@ -203,11 +246,43 @@ void server_loop(sse_server_s *s) {
                 }
                 if (group.empty()) break;
                 std::sort(group.begin(), group.end());  // arrival order
-                launch_round(s, group);
+                launch_round(s, lock, group);
             }
         }
         s->cv.wait_for(lock, std::chrono::microseconds(s->running.empty() ? 2000 : 50));
     }
+    s->thread_done = true;
+}
+
+// Cancel what has not started and stop admitting; requests that never ran end with
+// SSE_E_CANCELLED and stay pollable.  Called with the lock held.
+void cancel_unstarted(sse_server_s *s) {
+    s->stop = true;
+    const double t = now_ms();
+    for (uint64_t tk : s->pending) {
+        Request &q = s->reqs[tk];
+        q.state = kDone;
+        q.status = SSE_E_CANCELLED;
+        q.t_end = t;
+    }
+    s->pending.clear();
+    for (auto &kv : s->reqs)
+        if (kv.second.state == kAdmitted) {
+            kv.second.state = kDone;
+            kv.second.status = SSE_E_CANCELLED;
+            kv.second.t_end = t;
+            release(s, kv.second);
+        }
+}
+
+void free_server(sse_server_s *s) {
+    for (Slot &sl : s->slots) {
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    if (s->d_words) cudaFree(s->d_words);
+    if (s->h_words) cudaFreeHost(s->h_words);
+    delete s;
 }
 
 }  // namespace
@@ -225,20 +300,27 @@ SSE_API sse_status sse_server_create(uint64_t mem_budget_bytes, int32_t max_infl
     s->max_inflight = max_inflight;
     s->wait_limit_ms = wait_limit_ms ? wait_limit_ms : 1000;
     cudaGetDevice(&s->device);
-    for (int i = 0; i < 2; ++i) {
-        cudaError_t e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            if (i == 1) cudaStreamDestroy(s->streams[0]);
-            delete s;
-            return cuda_fail(e, "create server stream");
-        }
+    cudaError_t e = cudaMalloc(&s->d_words, 2 * kSlots * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_words, kSlots * sizeof(int32_t), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMemset(s->d_words, 0, 2 * kSlots * sizeof(int32_t));
+    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) {
+        Slot &sl = s->slots[i];
+        sl.d_words = s->d_words + 2 * i;
+        sl.h_status = s->h_words + i;
+        *sl.h_status = 0;
+        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        sse_status rs = cuda_fail(e, "create the server's streams and status words");
+        cudaGetLastError();
+        free_server(s);
+        return rs;
     }
     try {
         s->thread = std::thread(server_loop, s);
     } catch (...) {
-        cudaStreamDestroy(s->streams[0]);
-        cudaStreamDestroy(s->streams[1]);
-        delete s;
+        free_server(s);
         return set_error("could not start the server thread"), SSE_E_OUT_OF_MEMORY;
     }
     *out = s;
@@ -255,9 +337,9 @@ SSE_API sse_status sse_submit(sse_server_t *s, sse_plan_t *plan, const sse_io *i
     const uint64_t bytes = request_bytes(*p, *io);
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop) return set_error("server is shutting down"), SSE_E_SHUTDOWN;
-    if (bytes > s->budget)
-        return set_error("request needs %llu bytes, budget is %llu", (unsigned long long)bytes,
-                         (unsigned long long)s->budget),
+    if (bytes + plan_bytes(*p) > s->budget)
+        return set_error("request needs %llu bytes (buffers and plan workspace), budget is %llu",
+                         (unsigned long long)(bytes + plan_bytes(*p)), (unsigned long long)s->budget),
                SSE_E_OVER_BUDGET;
     const uint64_t tk = s->next_ticket++;
     Request q;
@@ -291,47 +373,35 @@ SSE_API sse_status sse_poll(sse_server_t *s, uint64_t ticket, sse_result *out) {
     return st;
 }
 
-SSE_API sse_status sse_server_destroy(sse_server_t *s) {
-    if (!s) return SSE_OK;
+SSE_API sse_status sse_server_shutdown(sse_server_t *s) {
+    if (!s) return set_error("server is NULL"), SSE_E_INVALID_ARG;
     {
         std::lock_guard<std::mutex> lock(s->mu);
-        s->stop = true;
-        // requests that never started are cancelled
-        for (uint64_t tk : s->pending) {
-            Request &q = s->reqs[tk];
-            q.state = kDone;
-            q.status = SSE_E_CANCELLED;
-        }
-        s->pending.clear();
-        for (auto &kv : s->reqs)
-            if (kv.second.state == kAdmitted) {
-                kv.second.state = kDone;
-                kv.second.status = SSE_E_CANCELLED;
-                s->inflight -= 1;
-                s->inflight_bytes -= kv.second.bytes;
-            }
+        cancel_unstarted(s);
     }
     s->cv.notify_one();
     // running rounds drain; give them the configured bound, then stop waiting
     const double t0 = now_ms();
-    sse_status rs = SSE_OK;
     while (true) {
         {
             std::lock_guard<std::mutex> lock(s->mu);
-            if (s->running.empty()) break;
+            if (s->thread_done) return SSE_OK;
         }
         if (now_ms() - t0 > s->wait_limit_ms) {
-            rs = SSE_E_TIMEOUT;
             set_error("rounds still running after %u ms at shutdown", s->wait_limit_ms);
-            break;
+            return SSE_E_TIMEOUT;
         }
+        s->cv.notify_one();
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
+}
+
+SSE_API sse_status sse_server_destroy(sse_server_t *s) {
+    if (!s) return SSE_OK;
+    const sse_status rs = sse_server_shutdown(s);
     if (rs == SSE_OK) {
         s->thread.join();
-        cudaStreamDestroy(s->streams[0]);
-        cudaStreamDestroy(s->streams[1]);
-        delete s;
+        free_server(s);
     } else {
         // the GPU still holds this server's work: keep the object alive (leaked) rather than
         // free streams and buffers under running kernels

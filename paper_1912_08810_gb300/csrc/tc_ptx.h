@@ -102,6 +102,13 @@ __device__ __forceinline__ void red_add_f2(float2 *p, float2 v) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// Fire-and-forget atomic add of an FP64 pair (two scalar reductions: PTX has no vector
+// form of red.add for f64).
+__device__ __forceinline__ void red_add_f64x2(double2 *p, double x, double y) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->x), "d"(x) : "memory");
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->y), "d"(y) : "memory");
+}
+
 // ---- bulk copies (TMA, non-tensor form) ------------------------------------------------
 
 // 1-D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global

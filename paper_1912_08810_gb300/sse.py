@@ -33,13 +33,17 @@ SSE_C64 = 1
 SSE_MODE_FP64 = 0
 SSE_MODE_MIXED = 1
 
+SSE_INJECT_NONE = 0
+SSE_INJECT_STALL = 1
+SSE_INJECT_ALLOC_FAIL = 2
+
 # Every function include/sse.h declares (checked by the CPU test suite).
 EXPORTED = (
     "sse_plan", "sse_plan_destroy", "sse_plan_query", "sse_execute", "sse_execute_host",
     "sse_plan_status", "sse_status_string", "sse_last_error", "sse_abi_version",
     "sse_execute_noalloc", "sse_execute_batch", "sse_batch_tuning",
-    "sse_server_create", "sse_submit", "sse_poll", "sse_server_destroy", "sse_server_stats",
-    "sse_plan_set_timing", "sse_plan_timing",
+    "sse_server_create", "sse_submit", "sse_poll", "sse_server_shutdown", "sse_server_destroy",
+    "sse_server_stats", "sse_plan_set_timing", "sse_plan_timing", "sse_debug_inject",
 )
 
 
@@ -107,7 +111,9 @@ def load(path: Optional[str] = None):
             "sse_server_create": ([ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(vp)], st),
             "sse_submit": ([vp, vp, ctypes.POINTER(sse_io), ctypes.POINTER(ctypes.c_uint64)], st),
             "sse_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(sse_result)], st),
+            "sse_server_shutdown": ([vp], st),
             "sse_server_destroy": ([vp], st),
+            "sse_debug_inject": ([st], st),
             "sse_server_stats": ([vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                   ctypes.POINTER(ctypes.c_int32)], st),
             "sse_plan_set_timing": ([vp, ctypes.c_int32], st),
@@ -223,6 +229,16 @@ def sse_poll(server, ticket: int):
     r = sse_result()
     rc = load().sse_poll(server, ticket, ctypes.byref(r))
     return rc, r
+
+
+def sse_server_shutdown(server) -> None:
+    """Cancel what has not started (pollable as SSE_E_CANCELLED), wait for running rounds."""
+    _check(load().sse_server_shutdown(server), "sse_server_shutdown")
+
+
+def sse_debug_inject(kind: int) -> None:
+    """Arm a one-shot test fault (SSE_INJECT_STALL or SSE_INJECT_ALLOC_FAIL; see include/sse.h)."""
+    _check(load().sse_debug_inject(kind), "sse_debug_inject")
 
 
 def sse_server_destroy(server) -> None:

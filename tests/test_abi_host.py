@@ -63,3 +63,16 @@ def test_bad_geometry_rejected_before_any_device_call(lib, field, value, msg):
     assert lib.sse_plan(ctypes.byref(g), ctypes.byref(h)) == sse.SSE_E_INVALID_ARG
     assert msg in sse.sse_last_error()
     assert not h.value
+
+
+def test_debug_inject_checks_its_argument(lib):
+    assert lib.sse_debug_inject(99) == sse.SSE_E_INVALID_ARG
+    assert "injection" in sse.sse_last_error()
+    assert lib.sse_debug_inject(sse.SSE_INJECT_ALLOC_FAIL) == sse.SSE_OK
+    assert lib.sse_debug_inject(sse.SSE_INJECT_NONE) == sse.SSE_OK  # disarmed again
+
+
+def test_server_entry_points_reject_null(lib):
+    assert lib.sse_server_shutdown(None) == sse.SSE_E_INVALID_ARG
+    assert lib.sse_server_destroy(None) == sse.SSE_OK
+    assert lib.sse_poll(None, 1, None) == sse.SSE_E_INVALID_ARG

@@ -110,3 +110,46 @@ def test_batch_rejects_inconsistent_plans():
     plans64, ios64, keep64 = setup([a], mode="fp64")
     with pytest.raises(sse.SSEError):
         sse.sse_execute_batch([p.handle for p in plans64], ios64, torch.cuda.current_stream().cuda_stream)
+
+
+def test_batched_workload_at_full_size():
+    """The batched workload itself (64 instances, Na ~ U[64,1024], NE ~ U[64,512], Nkz=Nqz=3,
+    Nw=16, 3..8 random neighbours, complex64, seed 3; about 139 GB of G and Sigma), evaluated
+    in one persistent launch and checked per instance against the oracle: the four smallest
+    instances in full and the largest on its first and last 16 atoms, both signs; every
+    instance's output finite and zero at E = 0."""
+    import torch
+    spec = inputs.BatchedSpec()
+    insts = inputs.make_batched_torch(spec, 3)
+    plans, ios, outs = [], [], []
+    for inst in insts:
+        g = inst["geometry"]
+        S = {s: torch.full_like(inst["G_gt"], float("nan")) for s in ("gt", "lt")}
+        p = sse.Plan(inst["neigh"], inst["dH"], nkz=g.nkz, nqz=g.nqz, ne=g.ne, nw=g.nw, mode="mixed")
+        ios.append(p._io(inst["G_gt"], inst["G_lt"], inst["D_gt"], inst["D_lt"], S["gt"], S["lt"]))
+        plans.append(p)
+        outs.append(S)
+    stream = torch.cuda.current_stream().cuda_stream
+    sse.sse_execute_batch([p.handle for p in plans], ios, stream)
+    torch.cuda.synchronize()
+    plans[0].status()
+    for S in outs:
+        for s in ("gt", "lt"):
+            assert bool(torch.isfinite(torch.view_as_real(S[s])).all())
+            assert bool((S[s][:, 0] == 0).all())
+    pts = [inst["geometry"].points() for inst in insts]
+    order = list(np.argsort(pts))
+    for i in order[:4] + order[-1:]:
+        inst = insts[i]
+        host = {k: inst[k].cpu().numpy() for k in ("G_gt", "G_lt", "D_gt", "D_lt", "dH", "neigh")}
+        na = inst["geometry"].na
+        ranges = [(0, na)] if i != order[-1] else [(0, 16), (na - 16, na)]
+        for s in ("gt", "lt"):
+            got = outs[i][s].cpu().numpy()
+            for a0, a1 in ranges:
+                ref = oracle.sigma_atoms(host["G_" + s], host["D_" + s], host["dH"], host["neigh"], a0, a1)
+                assert rel_fro(got[:, :, a0:a1], ref) <= TOL, (i, s, a0)
+    for p in plans:
+        p.close()
+    del insts, outs
+    torch.cuda.empty_cache()

@@ -103,31 +103,63 @@ def sampled_points(geo, n, seed):
     return pts
 
 
-def test_medium_config_sampled_points():
-    """Full medium workload (the benchmark's launch), checked on sampled output blocks
-    that the oracle evaluates one by one; plus whole-tensor invariants."""
+def test_medium_config_across_the_atom_axis():
+    """Full medium workload (the benchmark's launch: the warp-specialised form with units of
+    16 energy tiles) against the oracle element by element on five 16-atom ranges spread
+    over the atom axis (every (kz, E) of 80 atoms, both signs), plus sampled single blocks
+    and whole-tensor invariants."""
     geo = inputs.MEDIUM
     inst = inputs.make_instance(geo, 1)
     out = run(inst, "mixed")
+    ranges = [(0, 16), (120, 136), (248, 264), (376, 392), (496, 512)]
     pts = sampled_points(geo, 12, 0)
     for s in ("gt", "lt"):
-        ref = oracle.sigma_points(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], pts)
+        for a0, a1 in ranges:
+            ref = oracle.sigma_atoms(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], a0, a1)
+            assert rel_fro(out[s][:, :, a0:a1], ref) <= TOL, (s, a0)
+            assert max_block_rel(out[s][:, :, a0:a1], ref) <= 1e-3
+        refp = oracle.sigma_points(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], pts)
         got = np.stack([out[s][k, e, a] for k, e, a in pts])
-        assert rel_fro(got, ref) <= TOL
+        assert rel_fro(got, refp) <= TOL
         assert np.all(out[s][:, 0] == 0)
         assert np.all(np.isfinite(out[s]))
         assert rel_fro(out[s], -np.conj(np.swapaxes(out[s], -1, -2))) <= 2 * TOL
 
 
-def test_precision_config_atom_slice():
-    """Precision workload (Na = 2048, G about 6 GB per sign in complex128, seed 2):
-    the error is measured against the oracle on a slice of atoms plus sampled points."""
+def test_precision_config_128_atom_slice_both_signs():
+    """Precision workload (Na = 2048, G about 6 GB per sign in complex128, seed 2): the error
+    against the oracle on the Na = 128 atom slice, element by element, for both signs."""
     geo = inputs.PRECISION
     inst = inputs.make_instance(geo, 2)
-    out = run(inst, "mixed", signs=("gt",))
-    ref = oracle.sigma_atoms(inst["G_gt"], inst["D_gt"], inst["dH"], inst["neigh"], 0, 8)
-    assert rel_fro(out["gt"][:, :, 0:8], ref) <= TOL
-    pts = sampled_points(geo, 8, 1)
-    refp = oracle.sigma_points(inst["G_gt"], inst["D_gt"], inst["dH"], inst["neigh"], pts)
-    got = np.stack([out["gt"][k, e, a] for k, e, a in pts])
-    assert rel_fro(got, refp) <= TOL
+    out = run(inst, "mixed")
+    for s in ("gt", "lt"):
+        ref = oracle.sigma_atoms(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], 0, 128)
+        assert rel_fro(out[s][:, :, 0:128], ref) <= TOL, s
+        pts = sampled_points(geo, 8, 1)
+        refp = oracle.sigma_points(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"], pts)
+        got = np.stack([out[s][k, e, a] for k, e, a in pts])
+        assert rel_fro(got, refp) <= TOL
+
+
+@pytest.mark.parametrize("case", [
+    dict(ne=45, nw=32, na=9, nb=4, chain=True),    # ragged last tile, four slots per atom
+    dict(ne=20, nw=12, na=7, nb=6, chain=False),   # random slots incl. duplicates and self
+])
+def test_warp_specialised_form_complex64(case):
+    """Nkz = 5 with complex64 storage runs the warp-specialised kernel with float2 output:
+    the first slot's store and every later slot's FP32 reduction in place."""
+    geo = inputs.Geometry(nkz=5, nqz=5, ne=case["ne"], nw=case["nw"], na=case["na"], nb=case["nb"])
+    if case["chain"]:
+        inst = inputs.make_instance(geo, 71, dtype=np.complex64)
+    else:
+        rng = np.random.default_rng(72)
+        neigh = rng.integers(0, geo.na, size=(geo.na, geo.nb)).astype(np.int32)
+        neigh[0, 1] = -1
+        inst = inputs.make_instance(geo, 73, dtype=np.complex64, neigh=neigh, hermitian_pairs=False)
+    plans = []
+    out = run(inst, "mixed", plan_out=plans)
+    assert plans[0].info().workspace_bytes > 1024  # the warp-specialised form's workspace
+    plans[0].close()
+    for s in ("gt", "lt"):
+        assert rel_fro(out[s], oracle_full(inst, s)) <= TOL
+

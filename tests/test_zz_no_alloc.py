@@ -1,14 +1,16 @@
 """sse_execute_noalloc: the mixed-mode entry point for callers that cannot let the library
 allocate memory (for example a framework whose allocator owns all device memory).
 
-It must give the same Sigma as the planned path (sse_plan + sse_execute, mixed mode),
-call after call, even though every call reuses the same built-in scratch array.  This
+It must give the same Sigma as the planned path (sse_plan + sse_execute, mixed mode) and
+match the FP64 oracle, call after call, even though every call reuses the same built-in
+scratch array.  This
 file is collected last on purpose, so a failure here does not hide any other test."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1912_08810_gb300 import inputs, sse
 from tests.gpu_helpers import rel_fro, run, to_device
 
@@ -38,12 +40,14 @@ def test_matches_planned_path_on_two_calls_in_a_row(geo_seed):
     geo, seed, dt = geo_seed
     inst = inputs.make_instance(geo, seed, dtype=dt)
     ref = run(inst, "mixed")
+    exact = {s: oracle.sigma_atoms(inst["G_" + s], inst["D_" + s], inst["dH"], inst["neigh"]) for s in ("gt", "lt")}
     dev = to_device(inst)
     for _ in range(2):
         out = noalloc_call(dev, geo.nkz, geo.nqz, geo.ne, geo.nw)
         for s in ("gt", "lt"):
             assert np.all(np.isfinite(out[s]))
             assert rel_fro(out[s], ref[s]) <= TOL
+            assert rel_fro(out[s], exact[s]) <= TOL  # and against the FP64 oracle itself
 
 
 def test_rejects_what_it_cannot_run():
