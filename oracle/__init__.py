@@ -54,6 +54,10 @@ def _load():
                                                ctypes.c_int32, ctypes.c_int32, p]
             lib.oracle_sigma_atoms.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_dtilde.argtypes = [ctypes.POINTER(_Geometry), p, p, p]
+            lib.oracle_dtilde.restype = ctypes.c_int
+            lib.oracle_retarded.argtypes = [ctypes.c_int64, p, p, p]
+            lib.oracle_retarded.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -100,6 +104,35 @@ def sigma_atoms(G, Dt, dH, neigh, a_begin: int = 0, a_end=None, omega_first: int
                                     out.ctypes.data)
     if rc != 0:
         raise ValueError("oracle_sigma_atoms rejected its arguments")
+    return out
+
+
+def dtilde(D, neigh) -> np.ndarray:
+    """Pre-combined phonon term of Eq. 3 from the full tensor D [nqz, nw, na, nb+1, 3, 3]
+    (block nb = the diagonal D_aa); returns Dt [nqz, nw, na, nb, 3, 3]."""
+    D = _c128(D)
+    neigh = np.ascontiguousarray(neigh, dtype=np.int32)
+    nqz, nw, na, nb1, d1, d2 = D.shape
+    na2, nb = neigh.shape
+    if na2 != na or nb1 != nb + 1 or (d1, d2) != (3, 3):
+        raise ValueError("inconsistent D / neigh shapes")
+    geo = _Geometry(1, nqz, 1, nw, na, nb, 1, 0)
+    out = np.zeros((nqz, nw, na, nb, 3, 3), dtype=np.complex128)
+    rc = _load().oracle_dtilde(ctypes.byref(geo), neigh.ctypes.data, D.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_dtilde rejected its arguments (neighbour out of range or a bond without its reverse)")
+    return out
+
+
+def retarded(S_gt, S_lt) -> np.ndarray:
+    """Sigma^R = (Sigma^> - Sigma^<) / 2 (Section 2)."""
+    S_gt, S_lt = _c128(S_gt), _c128(S_lt)
+    if S_gt.shape != S_lt.shape:
+        raise ValueError("shape mismatch")
+    out = np.empty_like(S_gt)
+    rc = _load().oracle_retarded(S_gt.size, S_gt.ctypes.data, S_lt.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_retarded rejected its arguments")
     return out
 
 

@@ -24,7 +24,7 @@
  *  - Dt is the already pre-combined D_ba - D_bb - D_aa + D_ab (Section 3 input list);
  *  - Sigma is overwritten (accumulated into zero, the SCBA start value of Section 2).
  *
- * Two entry points:
+ * Entry points for Sigma:
  *  - oracle_sigma_points: the definition above, term by term, for chosen points;
  *  - oracle_sigma_atoms: the same sum after the paper's redundancy removal
  *    (Section 3, "Dataflow Optimizations": dH.G does not depend on (qz, w), so the
@@ -33,6 +33,9 @@
  *
  * Complex values are C99 `double complex`; all arithmetic is FP64; no BLAS; the
  * summation order is slot, i, j, q, w ascending in both entry points.
+ *
+ * The steps on either side of Sigma: oracle_dtilde (the phonon pre-combination of Eq. 3)
+ * and oracle_retarded (Sigma^R from Sigma^> and Sigma^<, Section 2).
  */
 #include <complex.h>
 #include <stdint.h>
@@ -198,6 +201,65 @@ int oracle_sigma_atoms(const oracle_geometry *g, const int32_t *neigh, const cpl
         free(x);
     }
     return bad ? -1 : 0;
+}
+
+/*
+ * The pre-combination of the phonon Green's function that Eq. 3 brackets, done before the
+ * Sigma kernel in Section 3 ("Dataflow Optimizations", the input list):
+ *   Dt[q,w,a,slot,i,j] = D_ba - D_bb - D_aa + D_ab,   b = neigh[a,slot],
+ * from the full phonon tensor D [nqz][nw][na][nb+1][3][3] of Section 2 (the shape with
+ * NB + 1 blocks per atom).  Readings taken here:
+ *  - block slot (< nb) of atom a is D_ab for b = neigh[a,slot]; block nb is the diagonal D_aa;
+ *  - D_ba is the block of atom b at the first slot s' with neigh[b,s'] = a; a bond whose
+ *    reverse is not listed makes the call fail (-1): Eq. 3 needs D_ba;
+ *  - an empty slot (neigh = -1) gives Dt = 0;
+ *  - the sum is taken in the order ((D_ba - D_bb) - D_aa) + D_ab.
+ * Dt is [nqz][nw][na][nb][3][3].  Returns 0 or -1.
+ */
+int oracle_dtilde(const oracle_geometry *g, const int32_t *neigh, const cplx *D, cplx *Dt) {
+    if (!valid_geometry(g) || !neigh || !D || !Dt) return -1;
+    const int nb = g->nb, nb1 = g->nb + 1;
+    for (int64_t p = 0; p < (int64_t)g->na * nb; ++p)
+        if (neigh[p] < -1 || neigh[p] >= g->na) return -1;
+    for (int a = 0; a < g->na; ++a)
+        for (int slot = 0; slot < nb; ++slot) {
+            const int b = neigh[(size_t)a * nb + slot];
+            if (b < 0) continue;
+            int rev = -1;
+            for (int s2 = 0; s2 < nb && rev < 0; ++s2)
+                if (neigh[(size_t)b * nb + s2] == a) rev = s2;
+            if (rev < 0) return -1;
+            for (int q = 0; q < g->nqz; ++q)
+                for (int w = 0; w < g->nw; ++w) {
+                    const size_t base = ((size_t)q * g->nw + w) * g->na;
+                    const cplx *d_ab = D + ((base + a) * nb1 + slot) * (N3D * N3D);
+                    const cplx *d_aa = D + ((base + a) * nb1 + nb) * (N3D * N3D);
+                    const cplx *d_ba = D + ((base + b) * nb1 + rev) * (N3D * N3D);
+                    const cplx *d_bb = D + ((base + b) * nb1 + nb) * (N3D * N3D);
+                    cplx *out = Dt + ((base + a) * nb + slot) * (N3D * N3D);
+                    for (int ij = 0; ij < N3D * N3D; ++ij)
+                        out[ij] = ((d_ba[ij] - d_bb[ij]) - d_aa[ij]) + d_ab[ij];
+                }
+        }
+    for (int a = 0; a < g->na; ++a)
+        for (int slot = 0; slot < nb; ++slot) {
+            if (neigh[(size_t)a * nb + slot] >= 0) continue;
+            for (int q = 0; q < g->nqz; ++q)
+                for (int w = 0; w < g->nw; ++w)
+                    memset(Dt + ((((size_t)q * g->nw + w) * g->na + a) * nb + slot) * (N3D * N3D), 0,
+                           sizeof(cplx) * N3D * N3D);
+        }
+    return 0;
+}
+
+/*
+ * The retarded self-energy from the lesser and greater ones (Section 2, the relation
+ * given after Eq. 5): Sigma^R = (Sigma^> - Sigma^<) / 2, elementwise over n complex values.
+ */
+int oracle_retarded(int64_t n, const cplx *S_gt, const cplx *S_lt, cplx *S_r) {
+    if (n < 0 || (n && (!S_gt || !S_lt || !S_r))) return -1;
+    for (int64_t x = 0; x < n; ++x) S_r[x] = (S_gt[x] - S_lt[x]) * 0.5;
+    return 0;
 }
 
 /* Threads the OpenMP runtime will use (1 without OpenMP). */
