@@ -56,6 +56,8 @@ def _load():
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_dtilde.argtypes = [ctypes.POINTER(_Geometry), p, p, p]
             lib.oracle_dtilde.restype = ctypes.c_int
+            lib.oracle_pi.argtypes = [ctypes.POINTER(_Geometry), p, p, p, p, p]
+            lib.oracle_pi.restype = ctypes.c_int
             lib.oracle_retarded.argtypes = [ctypes.c_int64, p, p, p]
             lib.oracle_retarded.restype = ctypes.c_int
             _lib = lib
@@ -133,6 +135,25 @@ def retarded(S_gt, S_lt) -> np.ndarray:
     rc = _load().oracle_retarded(S_gt.size, S_gt.ctypes.data, S_lt.ctypes.data, out.ctypes.data)
     if rc != 0:
         raise ValueError("oracle_retarded rejected its arguments")
+    return out
+
+
+def pi(Ga, Gb, dH, neigh, nqz: int, nw: int, omega_first: int = 1) -> np.ndarray:
+    """Phonon self-energy of Eqs. 4-5 with Ga paired at atom a (energy E + omega, momentum
+    k + q) and Gb at the neighbour (E, k): Pi^> = pi(G^>, G^<, ...), Pi^< = pi(G^<, G^>, ...).
+    Returns [nqz, nw, na, nb + 1, 3, 3] (block nb = the diagonal block)."""
+    Ga, Gb, dH = _c128(Ga), _c128(Gb), _c128(dH)
+    neigh = np.ascontiguousarray(neigh, dtype=np.int32)
+    nkz, ne, na, norb, _ = Ga.shape
+    nb = neigh.shape[1]
+    if Gb.shape != Ga.shape or dH.shape != (na, nb, 3, norb, norb) or neigh.shape[0] != na:
+        raise ValueError("inconsistent shapes")
+    geo = _Geometry(nkz, nqz, ne, nw, na, nb, norb, omega_first)
+    out = np.zeros((nqz, nw, na, nb + 1, 3, 3), dtype=np.complex128)
+    rc = _load().oracle_pi(ctypes.byref(geo), neigh.ctypes.data, dH.ctypes.data, Ga.ctypes.data,
+                           Gb.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_pi rejected its arguments")
     return out
 
 

@@ -35,7 +35,8 @@
  * summation order is slot, i, j, q, w ascending in both entry points.
  *
  * The steps on either side of Sigma: oracle_dtilde (the phonon pre-combination of Eq. 3)
- * and oracle_retarded (Sigma^R from Sigma^> and Sigma^<, Section 2).
+ * and oracle_retarded (Sigma^R from Sigma^> and Sigma^<, Section 2).  The phonon
+ * self-energy of Eqs. 4 and 5: oracle_pi.
  */
 #include <complex.h>
 #include <stdint.h>
@@ -260,6 +261,81 @@ int oracle_retarded(int64_t n, const cplx *S_gt, const cplx *S_lt, cplx *S_r) {
     if (n < 0 || (n && (!S_gt || !S_lt || !S_r))) return -1;
     for (int64_t x = 0; x < n; ++x) S_r[x] = (S_gt[x] - S_lt[x]) * 0.5;
     return 0;
+}
+
+/*
+ * The phonon scattering self-energy Pi^s (Eq. 5 for the off-diagonal blocks, Eq. 4 for the
+ * diagonal ones, Section 2), kept for the N_B neighbour couplings and the diagonal block
+ * as Section 2 states, in the shape of the phonon Green's function:
+ *   Pi [nqz][nw][na][nb + 1][3][3]   (block nb of an atom is its diagonal block).
+ * For a neighbour slot with b = neigh[a,slot] >= 0 (Eq. 5):
+ *   Pi[q,w,a,slot,i,j] = sum_{k < nkz} sum_{E : E' = E + (w + omega_first) < ne}
+ *       tr{ dH[a,slot,i]^dagger . Ga[(k + q) mod nkz, E', a] . dH[a,slot,j] . Gb[k, E, b] }
+ * and for the diagonal block (Eq. 4) the same trace summed over the neighbour slots with
+ * the opposite sign:
+ *   Pi[q,w,a,nb,i,j] = - sum_{slot : b >= 0} Pi[q,w,a,slot,i,j].
+ * Readings taken here (also in the design notes):
+ *  - the prefactors of Eqs. 4 and 5 (-i and +i) and the weight dE/2pi are left to the
+ *    caller (factor 1), keeping their relative sign: the diagonal block is minus the sum;
+ *  - Eq. 4's undefined sum index l is the neighbour b (as for Eq. 3);
+ *  - grad_i H_ba is the conjugate transpose of the stored dH[a,slot,i], grad_j H_ab = dH[a,slot,j];
+ *  - kz + qz wraps modulo nkz; E + omega above the energy grid contributes nothing;
+ *  - for Pi^> the caller passes Ga = G^> and Gb = G^< (G^{<>}_aa paired with G^{><}_bb), and
+ *    the reverse for Pi^<;
+ *  - an empty slot gives a zero block and adds nothing to the diagonal.
+ * The sums run k, E ascending; the diagonal block sums the slots ascending.  Returns 0 or -1.
+ */
+int oracle_pi(const oracle_geometry *g, const int32_t *neigh, const cplx *dH, const cplx *Ga, const cplx *Gb,
+              cplx *Pi) {
+    if (!valid_geometry(g) || !neigh || !dH || !Ga || !Gb || !Pi) return -1;
+    for (int64_t p = 0; p < (int64_t)g->na * g->nb; ++p)
+        if (neigh[p] < -1 || neigh[p] >= g->na) return -1;
+    const int n = g->norb, nn = n * n, nb = g->nb, nb1 = g->nb + 1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int a = 0; a < g->na; ++a) {
+        cplx *x = malloc(sizeof(cplx) * nn), *y = malloc(sizeof(cplx) * nn), *hi = malloc(sizeof(cplx) * nn);
+        if (!x || !y || !hi) { bad |= 1; free(x); free(y); free(hi); continue; }
+        for (int q = 0; q < g->nqz; ++q)
+            for (int w = 0; w < g->nw; ++w) {
+                cplx *diag = Pi + ((((size_t)q * g->nw + w) * g->na + a) * nb1 + nb) * (N3D * N3D);
+                for (int ij = 0; ij < N3D * N3D; ++ij) diag[ij] = 0;
+                for (int slot = 0; slot < nb; ++slot) {
+                    const int b = neigh[(size_t)a * nb + slot];
+                    cplx *blk = Pi + ((((size_t)q * g->nw + w) * g->na + a) * nb1 + slot) * (N3D * N3D);
+                    for (int i = 0; i < N3D; ++i)
+                        for (int j = 0; j < N3D; ++j) {
+                            cplx acc = 0;
+                            if (b >= 0) {
+                                const cplx *hI = dH + dh_index(g, a, slot, i), *hJ = dH + dh_index(g, a, slot, j);
+                                for (int r = 0; r < n; ++r)
+                                    for (int c = 0; c < n; ++c) hi[r * n + c] = conj(hI[c * n + r]); /* dH_i^dagger */
+                                for (int k = 0; k < g->nkz; ++k)
+                                    for (int e = 0; e < g->ne; ++e) {
+                                        const int ep = e + w + g->omega_first;
+                                        if (ep >= g->ne) continue; /* E + omega above the energy grid */
+                                        const int kq = (k + q) % g->nkz;
+                                        matmul(n, hi, Ga + g_index(g, kq, ep, a), x);  /* dH_i^+ . Ga      */
+                                        matmul(n, x, hJ, y);                            /* ... . dH_j       */
+                                        const cplx *gb = Gb + g_index(g, k, e, b);
+                                        for (int r = 0; r < n; ++r)                     /* tr{ ... . Gb }   */
+                                            for (int c = 0; c < n; ++c) acc += y[r * n + c] * gb[c * n + r];
+                                    }
+                            }
+                            blk[i * N3D + j] = acc;
+                        }
+                }
+                for (int slot = 0; slot < nb; ++slot) {
+                    if (neigh[(size_t)a * nb + slot] < 0) continue;
+                    const cplx *blk = Pi + ((((size_t)q * g->nw + w) * g->na + a) * nb1 + slot) * (N3D * N3D);
+                    for (int ij = 0; ij < N3D * N3D; ++ij) diag[ij] -= blk[ij];
+                }
+            }
+        free(x);
+        free(y);
+        free(hi);
+    }
+    return bad ? -1 : 0;
 }
 
 /* Threads the OpenMP runtime will use (1 without OpenMP). */
