@@ -65,7 +65,8 @@ enum {
     SSE_E_TIMEOUT = -5,         /* a bounded device or host wait expired */
     SSE_E_UNKNOWN_TICKET = -6,  /* sse_poll: no such ticket (or already collected) */
     SSE_E_SHUTDOWN = -7,        /* the server is shutting down or was destroyed */
-    SSE_E_CANCELLED = -9        /* the request was cancelled before it ran */
+    SSE_E_CANCELLED = -9,       /* the request was cancelled before it ran */
+    SSE_E_BOUNDS = -10          /* bounds-checked build only: a kernel computed an index outside a buffer */
 };
 
 typedef enum { SSE_C128 = 0, SSE_C64 = 1 } sse_dtype;
@@ -123,6 +124,50 @@ SSE_API sse_status sse_plan_query(const sse_plan_t *plan, sse_plan_info *info);
 /* Enqueue Sigma^> and/or Sigma^< for one instance on `stream` (asynchronous, stream
  * ordered).  io buffers must follow the plan's geometry and dtype. */
 SSE_API sse_status sse_execute(sse_plan_t *plan, const sse_io *io, void *stream);
+
+/* ---- the steps on either side of Sigma -----------------------------------------------------
+ *
+ * The full phonon tensor D^s of Section 2 is [nqz][nw][na][nb_max + 1][3][3]: block slot
+ * (< nb_max) of atom a couples a to b = neigh[a][slot] (D_ab), block nb_max is the diagonal
+ * D_aa.  Eq. 3 uses the pre-combination (Section 3, "Dataflow Optimizations", input list)
+ *   Dt[q][w][a][slot] = D_ba - D_bb - D_aa + D_ab,
+ * where D_ba is the block of b at the first slot s' with neigh[b][s'] = a.  A plan whose
+ * neighbour list has a bond without its reverse cannot form it (SSE_E_INVALID_ARG).  Dt is
+ * summed in FP64 in the order ((D_ba - D_bb) - D_aa) + D_ab and rounded once to the plan's
+ * dtype; an empty slot gives 0. */
+
+/* Pre-combine one sign: D device [nqz][nw][na][nb_max + 1][3][3] -> Dt device
+ * [nqz][nw][na][nb_max][3][3], both in the plan's dtype.  Asynchronous on `stream`. */
+SSE_API sse_status sse_dtilde(const sse_plan_t *plan, const void *D, void *Dt, void *stream);
+
+/* The retarded component (Section 2, the relation after Eq. 5): S_r = (S_gt - S_lt) / 2,
+ * elementwise over the plan's Sigma shape [nkz][ne][na][12][12].  Asynchronous. */
+SSE_API sse_status sse_retarded(const sse_plan_t *plan, const void *S_gt, const void *S_lt, void *S_r, void *stream);
+
+/* The chain from the phonon Green's function to Sigma^R on `stream`: io->D_gt / io->D_lt hold
+ * the FULL phonon tensors [nqz][nw][na][nb_max + 1][3][3]; Sigma^> and Sigma^< are written as
+ * by sse_execute, and Sigma^R as well when S_r is not NULL (both signs needed then).  The
+ * mixed form pre-combines Dt where its kernels read it (the tensor is never stored; results
+ * equal sse_dtilde followed by sse_execute bit for bit); the FP64 form pre-combines into
+ * plan-owned scratch (2 x the Dt size, allocated on first use, reported in workspace_bytes). */
+SSE_API sse_status sse_execute_full(sse_plan_t *plan, const sse_io *io, void *S_r, void *stream);
+
+/* ---- the phonon self-energy ----------------------------------------------------------------
+ *
+ * Pi^> and/or Pi^< of Eq. 5 (the N_B off-diagonal blocks, Section 2 keeps these) and Eq. 4
+ * (the diagonal block), on the plan's geometry:
+ *   Pi^s[q][w][a][slot][i][j] = sum_k sum_{E : E' = E + (w + omega_first) < ne}
+ *       tr{ dH[a][slot][i]^dagger . G^s[(k + q) mod nkz][E'][a] . dH[a][slot][j] . G^s'[k][E][b] }
+ * for b = neigh[a][slot] >= 0 (zero block for an empty slot), s' the opposite sign of s, and
+ *   Pi^s[q][w][a][nb_max][i][j] = - sum over the atom's non-empty slots of the above.
+ * Readings: the prefactors -i (Eq. 4) and +i (Eq. 5) and the weight dE/2pi are the caller's,
+ * their relative sign kept (the diagonal block is minus the sum); Eq. 4's index l is the
+ * neighbour; grad_i H_ba = dH[a][slot][i]^dagger; kz + qz wraps modulo nkz; E + omega above
+ * the energy grid contributes nothing.  Layout: Pi [nqz][nw][na][nb_max + 1][3][3] in the plan's
+ * dtype (the shape of the full phonon Green's function).  Both G^> and G^< are read for either
+ * sign.  FP64 arithmetic on the FP64 pipe, whatever the plan's mode; nw <= 90.  Asynchronous
+ * on `stream`; a NULL Pi pointer skips that sign. */
+SSE_API sse_status sse_pi(sse_plan_t *plan, const void *G_gt, const void *G_lt, void *Pi_gt, void *Pi_lt, void *stream);
 
 /* Same computation with HOST buffers (pageable or pinned): copies the inputs to
  * plan-owned device staging on `stream`, runs, copies Sigma back and synchronises
@@ -199,7 +244,9 @@ SSE_API sse_status sse_server_stats(sse_server_t *server, uint64_t *rounds, uint
                                     int32_t *inflight);
 
 /* Synchronise the plan's last stream and read (then clear) the device status word that
- * its kernels write: SSE_OK, or SSE_E_TIMEOUT if a bounded device wait expired. */
+ * its kernels write: SSE_OK, SSE_E_TIMEOUT if a bounded device wait expired, or (only in
+ * the bounds-checked build, libsse_gb300_bc.so) SSE_E_BOUNDS if a kernel computed an index
+ * outside one of its buffers and skipped that access. */
 SSE_API sse_status sse_plan_status(sse_plan_t *plan);
 
 /* Kernel timing of sse_execute on one plan, for benchmarks and profiling; the paper has no

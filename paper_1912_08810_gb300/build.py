@@ -2,6 +2,9 @@
 
 Each .cu file under csrc/ compiles in its own nvcc process (in parallel), then nvcc
 links the shared library next to this file.  Objects go to _build/ (git-ignored).
+build(bounds_check=True) makes the bounds-checked variant, libsse_gb300_bc.so (objects in
+_build_bc/): the same sources compiled with -DSSE_BOUNDS_CHECK, whose kernels check every
+global index they compute and report violations through the status word.
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsse_gb300.so")
+BUILD_BC = os.path.join(HERE, "_build_bc")
+LIB_BC = os.path.join(HERE, "libsse_gb300_bc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -36,16 +41,18 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile every csrc/*.cu and link libsse_gb300.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=None, bounds_check: bool = False) -> str:
+    """Compile every csrc/*.cu and link libsse_gb300.so (or, with bounds_check, the
+    bounds-checked libsse_gb300_bc.so); returns its path."""
+    bdir, lib = (BUILD_BC, LIB_BC) if bounds_check else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DSSE_BOUNDS_CHECK"] if bounds_check else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers + [__file__]):
             cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
             if verbose:
@@ -59,13 +66,20 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    if force or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcuda"]
+    if force or _stale(lib, objs):
+        cmd = [nvcc, *ARCH, "-shared", "-o", lib + ".tmp", *objs, "-lcuda"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
+
+
+def build_all(force: bool = False) -> None:
+    """Both libraries, their compilations run side by side."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        for f in [ex.submit(build, force), ex.submit(build, force, False, None, True)]:
+            f.result()
 
 
 if __name__ == "__main__":

@@ -157,6 +157,7 @@ const char *sse_status_string(sse_status s) {
         case SSE_E_UNKNOWN_TICKET: return "SSE_E_UNKNOWN_TICKET";
         case SSE_E_SHUTDOWN: return "SSE_E_SHUTDOWN";
         case SSE_E_CANCELLED: return "SSE_E_CANCELLED";
+        case SSE_E_BOUNDS: return "SSE_E_BOUNDS";
         default: return "SSE_E_UNKNOWN_STATUS";
     }
 }
@@ -192,25 +193,42 @@ sse_status sse_plan(const sse_geometry *geo, sse_plan_t **out) {
         }
     }
     p->cmacs_per_sign = algorithmic_cmacs(p->d, p->neigh_host);
+    // reverse bonds (for the phonon pre-combination of Eq. 3)
+    std::vector<int32_t> rev(nn, -1);
+    p->rev_ok = true;
+    for (int a = 0; a < geo->na; ++a)
+        for (int s = 0; s < geo->nb_max; ++s) {
+            const int32_t b = p->neigh_host[(size_t)a * geo->nb_max + s];
+            if (b < 0) continue;
+            for (int s2 = 0; s2 < geo->nb_max && rev[(size_t)a * geo->nb_max + s] < 0; ++s2)
+                if (p->neigh_host[(size_t)b * geo->nb_max + s2] == a) rev[(size_t)a * geo->nb_max + s] = s2;
+            if (rev[(size_t)a * geo->nb_max + s] < 0) p->rev_ok = false;
+        }
     {
         size_t valid = 0;
         for (int32_t f : p->neigh_host) valid += f >= 0;
         p->slots_per_atom = (double)valid / geo->na;
     }
     e = cudaMalloc(&p->d_status, sizeof(int32_t));
+    if (e == cudaSuccess) {
+        e = cudaMalloc(&p->d_rev, nn * sizeof(int32_t));
+        if (e != cudaSuccess) cudaFree(p->d_status);
+    }
     if (e != cudaSuccess) {
         delete p;
-        return e == cudaErrorMemoryAllocation ? (set_error("cudaMalloc status word"), SSE_E_OUT_OF_MEMORY)
-                                              : cuda_fail(e, "cudaMalloc status word");
+        return e == cudaErrorMemoryAllocation ? (set_error("cudaMalloc of the plan's small tables"), SSE_E_OUT_OF_MEMORY)
+                                              : cuda_fail(e, "cudaMalloc of the plan's small tables");
     }
     cudaMemset(p->d_status, 0, sizeof(int32_t));
-    p->workspace_bytes = sizeof(int32_t);
+    cudaMemcpy(p->d_rev, rev.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice);
+    p->workspace_bytes = sizeof(int32_t) + (int64_t)(nn * sizeof(int32_t));
     if (geo->mode == SSE_MODE_MIXED) {
         p->kernel_id = 1;
         st = mixed_plan_init(*p);
         if (st != SSE_OK) {
             mixed_plan_free(*p);
             cudaFree(p->d_status);
+            cudaFree(p->d_rev);
             delete p;
             return st;
         }
@@ -228,6 +246,8 @@ sse_status sse_plan_destroy(sse_plan_t *plan) {
     mixed_plan_free(*plan);
     timing_free(plan->timing);
     if (plan->d_status) cudaFree(plan->d_status);
+    if (plan->d_rev) cudaFree(plan->d_rev);
+    if (plan->dt_scratch) cudaFree(plan->dt_scratch);
     if (plan->staging) cudaFree(plan->staging);
     delete plan;
     return SSE_OK;
@@ -242,7 +262,7 @@ sse_status sse_plan_query(const sse_plan_t *plan, sse_plan_info *info) {
     info->points = (int64_t)d.nkz * d.ne * d.na;
     info->flops_per_sign = 8.0 * plan->cmacs_per_sign;
     info->bytes_per_sign = eb * (2.0 * g_elems(d) + d_elems(d) + 0.5 * dh_elems(d)) + 0.5 * 4.0 * d.na * d.nb;
-    info->workspace_bytes = plan->workspace_bytes + (int64_t)plan->staging_bytes;
+    info->workspace_bytes = plan->workspace_bytes + (int64_t)plan->staging_bytes + (int64_t)plan->dt_scratch_bytes;
     info->tile_e = plan->tile_e;
     info->kernel_id = plan->kernel_id;
     return SSE_OK;
@@ -265,6 +285,75 @@ sse_status sse_execute(sse_plan_t *plan, const sse_io *io, void *stream) {
     sse_status st = check_io(*plan, io);
     if (st != SSE_OK) return st;
     return dispatch(plan, *io, (cudaStream_t)stream);
+}
+
+sse_status sse_dtilde(const sse_plan_t *plan, const void *D, void *Dt, void *stream) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    if (!device_pointer(D) || !device_pointer(Dt)) return set_error("D and Dt must be device pointers"), SSE_E_INVALID_ARG;
+    return launch_dtilde(*plan, D, Dt, (cudaStream_t)stream);
+}
+
+sse_status sse_retarded(const sse_plan_t *plan, const void *S_gt, const void *S_lt, void *S_r, void *stream) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    if (!device_pointer(S_gt) || !device_pointer(S_lt) || !device_pointer(S_r))
+        return set_error("S_gt, S_lt and S_r must be device pointers"), SSE_E_INVALID_ARG;
+    return launch_retarded(*plan, S_gt, S_lt, S_r, (cudaStream_t)stream);
+}
+
+sse_status sse_pi(sse_plan_t *plan, const void *G_gt, const void *G_lt, void *Pi_gt, void *Pi_lt, void *stream) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    if (!Pi_gt && !Pi_lt) return SSE_OK;
+    if (!device_pointer(G_gt) || !device_pointer(G_lt))
+        return set_error("G_gt and G_lt must both be device pointers (each sign of Pi pairs one with the other)"),
+               SSE_E_INVALID_ARG;
+    if ((Pi_gt && !device_pointer(Pi_gt)) || (Pi_lt && !device_pointer(Pi_lt)))
+        return set_error("Pi_gt / Pi_lt must be device pointers"), SSE_E_INVALID_ARG;
+    plan->last_stream = (cudaStream_t)stream;
+    return launch_pi(*plan, G_gt, G_lt, Pi_gt, Pi_lt, (cudaStream_t)stream);
+}
+
+sse_status sse_execute_full(sse_plan_t *plan, const sse_io *io, void *S_r, void *stream) {
+    if (!plan) return set_error("plan is NULL"), SSE_E_INVALID_ARG;
+    sse_status rs = check_io(*plan, io);
+    if (rs != SSE_OK) return rs;
+    if (!plan->rev_ok) {
+        set_error("the pre-combination needs every bond's reverse: some neigh[a][slot] = b has no slot of b holding a");
+        return SSE_E_INVALID_ARG;
+    }
+    if (S_r && (!io->S_gt || !io->S_lt)) return set_error("Sigma^R needs both signs"), SSE_E_INVALID_ARG;
+    if (S_r && !device_pointer(S_r)) return set_error("S_r must be a device pointer"), SSE_E_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    plan->last_stream = st;
+    if (plan->kernel_id == 1) {
+        rs = launch_mixed(*plan, *io, st, /*dfull=*/true);
+    } else {
+        // the FP64 form reads Dt in its innermost loop: pre-combine into plan-owned scratch
+        const size_t db = d_elems(plan->d) * elem_bytes(plan->geo.dtype);
+        if (plan->dt_scratch_bytes < 2 * db) {
+            if (plan->dt_scratch) cudaFree(plan->dt_scratch);
+            plan->dt_scratch = nullptr;
+            plan->dt_scratch_bytes = 0;
+            cudaError_t e = take_inject(SSE_INJECT_ALLOC_FAIL) ? cudaErrorMemoryAllocation : cudaMalloc(&plan->dt_scratch, 2 * db);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                plan->dt_scratch = nullptr;
+                return set_error("cudaMalloc of %zu bytes for Dt failed", 2 * db), SSE_E_OUT_OF_MEMORY;
+            }
+            plan->dt_scratch_bytes = 2 * db;
+        }
+        sse_io dio = *io;
+        if (io->S_gt) {
+            rs = launch_dtilde(*plan, io->D_gt, plan->dt_scratch, st);
+            dio.D_gt = plan->dt_scratch;
+        }
+        if (rs == SSE_OK && io->S_lt) {
+            rs = launch_dtilde(*plan, io->D_lt, (char *)plan->dt_scratch + db, st);
+            dio.D_lt = (char *)plan->dt_scratch + db;
+        }
+        if (rs == SSE_OK) rs = dispatch(plan, dio, st);
+    }
+    if (rs == SSE_OK && S_r) rs = launch_retarded(*plan, io->S_gt, io->S_lt, S_r, st);
+    return rs;
 }
 
 sse_status sse_execute_host(sse_plan_t *plan, const sse_io *h, void *stream) {
@@ -402,6 +491,10 @@ sse_status sse_plan_status(sse_plan_t *plan) {
     if (e != cudaSuccess) return cuda_fail(e, "read plan status");
     if (v != 0) {
         cudaMemset(plan->d_status, 0, sizeof v);
+        if (v & kStatusBounds) {
+            set_error("a kernel of this plan computed an index outside one of its buffers (status %d)", v);
+            return SSE_E_BOUNDS;
+        }
         set_error("a device-side wait of this plan expired (code %d)", v);
         return SSE_E_TIMEOUT;
     }

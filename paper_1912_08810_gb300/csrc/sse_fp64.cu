@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kThreads)
 sse_fp64_direct_kernel(const int32_t *__restrict__ neigh, const CT *__restrict__ dH,
                        const CT *__restrict__ G0, const CT *__restrict__ D0, CT *__restrict__ S0,
                        const CT *__restrict__ G1, const CT *__restrict__ D1, CT *__restrict__ S1,
-                       Dims d) {
+                       Dims d, int32_t *status) {
     __shared__ double2 s_dh[kN3D][kBlk];
     __shared__ double2 s_y[kN3D * kN3D][kBlk];
     __shared__ double2 s_z[kN3D][kBlk];
@@ -81,6 +81,7 @@ sse_fp64_direct_kernel(const int32_t *__restrict__ neigh, const CT *__restrict__
     for (int slot = 0; slot < d.nb; ++slot) {
         const int f = __ldg(neigh + (size_t)a * d.nb + slot);
         if (f < 0) continue;  // empty slot (uniform over the CTA)
+        if (!SSE_BC(f, d.na, status)) continue;
         const CT *dh = dH + ((size_t)a * d.nb + slot) * kN3D * kBlk;
         for (int x = threadIdx.x; x < kN3D * kBlk; x += kThreads) s_dh[x / kBlk][x % kBlk] = ld(dh + x);
 
@@ -96,8 +97,12 @@ sse_fp64_direct_kernel(const int32_t *__restrict__ neigh, const CT *__restrict__
                 for (int w = 0; w < d.nw; ++w) {
                     const int ep = e - w - d.omega_first;
                     if (ep < 0) break;  // every later w is further below the grid
-                    const double2 g = ld(gq + (size_t)ep * d.na * kBlk);
+                    const CT *gp = gq + (size_t)ep * d.na * kBlk;
                     const CT *dw = dq + (size_t)w * d.na * d.nb * 9;
+                    if (!SSE_BC(gp - G, (long long)d.nkz * d.ne * d.na * kBlk, status) ||
+                        !SSE_BC(dw + 8 - D, (long long)d.nqz * d.nw * d.na * d.nb * 9, status))
+                        continue;
+                    const double2 g = ld(gp);
 #pragma unroll
                     for (int ij = 0; ij < 9; ++ij) cmac(y[ij], ld(dw + ij), g);
                 }
@@ -128,7 +133,8 @@ sse_fp64_direct_kernel(const int32_t *__restrict__ neigh, const CT *__restrict__
         }
         __syncthreads();
     }
-    if (active) st(S + (size_t)p * kBlk + c, acc);
+    if (active && SSE_BC((size_t)p * kBlk + c, (long long)d.nkz * d.ne * d.na * kBlk, status))
+        st(S + (size_t)p * kBlk + c, acc);
 }
 
 }  // namespace
@@ -151,13 +157,13 @@ sse_status launch_fp64_direct(const Plan &p, const sse_io &io, cudaStream_t st) 
         double2 *s0 = (double2 *)(do_gt ? io.S_gt : io.S_lt);
         sse_fp64_direct_kernel<double2><<<grid, kThreads, 0, st>>>(
             p.geo.neigh, (const double2 *)p.geo.dH, g0, d0, s0, (const double2 *)io.G_lt,
-            (const double2 *)io.D_lt, (double2 *)io.S_lt, d);
+            (const double2 *)io.D_lt, (double2 *)io.S_lt, d, p.d_status);
     } else {
         const float2 *g0 = (const float2 *)(do_gt ? io.G_gt : io.G_lt), *d0 = (const float2 *)(do_gt ? io.D_gt : io.D_lt);
         float2 *s0 = (float2 *)(do_gt ? io.S_gt : io.S_lt);
         sse_fp64_direct_kernel<float2><<<grid, kThreads, 0, st>>>(
             p.geo.neigh, (const float2 *)p.geo.dH, g0, d0, s0, (const float2 *)io.G_lt,
-            (const float2 *)io.D_lt, (float2 *)io.S_lt, d);
+            (const float2 *)io.D_lt, (float2 *)io.S_lt, d, p.d_status);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch sse_fp64_direct_kernel");

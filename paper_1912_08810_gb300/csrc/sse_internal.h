@@ -12,6 +12,22 @@
 
 namespace sse {
 
+// Bounds-checked build (compiled with -DSSE_BOUNDS_CHECK into a library of its own): each
+// global index a kernel computes is checked against the extent of its buffer; a violation
+// sets kStatusBounds in the status word (read by sse_plan_status as SSE_E_BOUNDS) and the
+// access is skipped.  Nothing traps.  In the normal build the checks compile away.
+constexpr int32_t kStatusTimeout = 1, kStatusBounds = 2;
+#ifdef SSE_BOUNDS_CHECK
+__device__ __forceinline__ bool bc_in(long long idx, long long n, int32_t *status) {
+    const bool ok = idx >= 0 && idx < n;
+    if (!ok && status) atomicOr(status, kStatusBounds);
+    return ok;
+}
+#define SSE_BC(idx, n, status) ::sse::bc_in((long long)(idx), (long long)(n), (status))
+#else
+#define SSE_BC(idx, n, status) true
+#endif
+
 constexpr int kNorb = 12;             // orbitals per atom (the only size the kernels take)
 constexpr int kBlk = kNorb * kNorb;   // complex values per norb x norb block
 constexpr int kN3D = 3;               // vibration directions i, j
@@ -47,6 +63,14 @@ struct Plan {
     // then the slot tables of every (atom, slot)
     void *mixed_ws = nullptr;
     size_t mixed_ws_bytes = 0;
+    // Reverse bonds for the phonon pre-combination (Eq. 3): rev[a][slot] = the first slot s'
+    // of b = neigh[a][slot] with neigh[b][s'] = a; -1 for an empty slot or a bond whose
+    // reverse is not listed (rev_ok is then false).
+    int32_t *d_rev = nullptr;
+    bool rev_ok = false;
+    // Dt of both signs for the FP64 form of sse_execute_full (allocated on first use)
+    void *dt_scratch = nullptr;
+    size_t dt_scratch_bytes = 0;
     KernelTiming timing;
 };
 
@@ -70,7 +94,14 @@ double algorithmic_cmacs(const Dims &d, const std::vector<int32_t> &neigh_host);
 
 // Kernel launchers (return SSE_OK or an error after set_error).
 sse_status launch_fp64_direct(const Plan &p, const sse_io &io, cudaStream_t st);
-sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st);
+// dfull: io.D_gt / io.D_lt hold the full phonon tensors [nqz][nw][na][nb+1][3][3]; the
+// kernels then form Dt = D_ba - D_bb - D_aa + D_ab where they read it (needs p.rev_ok).
+sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st, bool dfull = false);
+// The steps on either side (sse_edges.cu): Dt of one sign into `dt`, Sigma^R from both signs.
+sse_status launch_dtilde(const Plan &p, const void *D, void *dt, cudaStream_t st);
+sse_status launch_retarded(const Plan &p, const void *S_gt, const void *S_lt, void *S_r, cudaStream_t st);
+// The phonon self-energy of Eqs. 4-5 (sse_pi.cu), FP64.
+sse_status launch_pi(const Plan &p, const void *G_gt, const void *G_lt, void *Pi_gt, void *Pi_lt, cudaStream_t st);
 // Persistent launch over n instances in the given order (all plans mixed, with equal
 // nkz, nw, omega_first and dtype), `tpc` tiles per work unit, `queue` a device counter;
 // expired device waits are recorded in the device word `status`.

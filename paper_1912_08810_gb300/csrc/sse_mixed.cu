@@ -86,6 +86,7 @@ struct InstDesc {
     int32_t nchunks;        // units per (sign, atom)
     int32_t nsign;
     long long unit_begin;
+    const int32_t *rev;     // non-null: D holds the full phonon tensors and Dt is formed on the fly
     const uint8_t *gws[2];  // tensor-core form: G re-encoded per sign (see sse_split_g_kernel)
     const uint8_t *sws[2];  // tensor-core form: slot tables per sign (see sse_slot_tables_kernel)
 };
@@ -101,6 +102,36 @@ struct MixParams {
     uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, off_x, off_bp, g_stage;
     InstDesc inst[kMaxInst];
 };
+
+template <typename CT>
+__device__ __forceinline__ double2 ld_c64(const CT *p);
+template <>
+__device__ __forceinline__ double2 ld_c64<double2>(const double2 *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ double2 ld_c64<float2>(const float2 *p) {
+    const float2 v = __ldg(p);
+    return make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
+}
+
+// Entry ij of Dt[q, w, a, b] in FP32.  Without `rev`, D holds Dt [nqz][nw][na][nb][3][3];
+// with it, D holds the full phonon tensor [nqz][nw][na][nb + 1][3][3] (block nb = D_aa) and
+// the pre-combination of Eq. 3, Dt = ((D_ba - D_bb) - D_aa) + D_ab with D_ba the block of
+// f = neigh[a, b] at its slot rev[a, b], is formed here in FP64 and rounded once -- the
+// same value the stand-alone pre-combination kernel stores.  Only for slots with f >= 0.
+template <typename CT>
+__device__ __forceinline__ float2 load_dt(const CT *__restrict__ D, const int32_t *__restrict__ neigh,
+                                          const int32_t *__restrict__ rev, int q, int w, int nw, int na, int nb,
+                                          int a, int b, int ij, int32_t *status) {
+    if (!rev) return load_c32(D + ((((size_t)q * nw + w) * na + a) * nb + b) * 9 + ij);
+    const size_t qw = ((size_t)q * nw + w) * na;
+    const int f = __ldg(neigh + (size_t)a * nb + b), r = __ldg(rev + (size_t)a * nb + b);
+    if (!SSE_BC(f, na, status) || !SSE_BC(r, nb, status)) return make_float2(0.f, 0.f);
+    const size_t nb1 = (size_t)nb + 1;
+    const double2 ab = ld_c64(D + ((qw + a) * nb1 + b) * 9 + ij), aa = ld_c64(D + ((qw + a) * nb1 + nb) * 9 + ij);
+    const double2 ba = ld_c64(D + ((qw + f) * nb1 + r) * 9 + ij), bb = ld_c64(D + ((qw + f) * nb1 + nb) * 9 + ij);
+    const double x = ((ba.x - bb.x) - aa.x) + ab.x, y = ((ba.y - bb.y) - aa.y) + ab.y;
+    return make_float2(f64_to_f32(x), f64_to_f32(y));
+}
 
 __device__ __forceinline__ float2 cmul_conj_acc(float2 acc, float2 v, float2 h) {
     // acc + v * conj(h)
@@ -375,9 +406,12 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         for (int p = 0; p < GG::P; ++p) {
             const int Ep = e_first + p;
             if (Ep < 0 || Ep >= d.ne) continue;
-            for (int kp = 0; kp < NK; ++kp)
-                bulk_g2s(dst + (p * NK + kp) * kCh * sizeof(CT),
-                         G + (((size_t)kp * d.ne + Ep) * d.na + f) * kCh, kCh * (uint32_t)sizeof(CT), bar);
+            for (int kp = 0; kp < NK; ++kp) {
+                const size_t src = (((size_t)kp * d.ne + Ep) * d.na + f) * kCh;
+                // a skipped copy leaves the stage's barrier short: its wait then times out
+                if (SSE_BC(src + kCh - 1, (long long)d.nkz * d.ne * d.na * kCh, prm.status))
+                    bulk_g2s(dst + (p * NK + kp) * kCh * sizeof(CT), G + src, kCh * (uint32_t)sizeof(CT), bar);
+            }
         }
     };
 
@@ -401,14 +435,16 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
             // job's MMAs are complete, so the B (and A) stages are free scratch.
             const int b = s_slot[vs];
             const CT *dh = dH + ((size_t)a * d.nb + b) * 3 * kCh;
-            for (int x = tid; x < 3 * kCh; x += kThreads) sDh[x] = load_c32(dh + x);
+            for (int x = tid; x < 3 * kCh; x += kThreads)
+                sDh[x] = SSE_BC((dh - dH) + x, (long long)d.na * d.nb * 3 * kCh, prm.status) ? load_c32(dh + x)
+                                                                                           : make_float2(0.f, 0.f);
             float2 *dfold = (float2 *)sB;  // [kappa][w][ij] folded Dt (fp32), A/B area as scratch
             for (int x = tid; x < NK * nw * 9; x += kThreads) {
                 const int ij = x % 9, w = (x / 9) % nw, kap = x / (9 * nw);
                 // fold qz onto kz' = qz mod Nkz: T depends on (k - k') mod Nkz only
                 float2 acc = make_float2(0.f, 0.f);
                 for (int q = kap; q < d.nqz; q += NK) {
-                    const float2 v = load_c32(D + ((((size_t)q * nw + w) * d.na + a) * d.nb + b) * 9 + ij);
+                    const float2 v = load_dt(D, I.neigh, I.rev, q, w, nw, d.na, d.nb, a, b, ij, prm.status);
                     acc.x += v.x;
                     acc.y += v.y;
                 }
@@ -494,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         // ---- G blocks of this stage: wait, convert to fp32 in place, zero the gaps ----
         if (!mbar_wait_bounded(&bar_g[sb], (gg >> 1) & 1, kWaitNs)) {
             *s_abort = 1;
-            atomicExch(prm.status, 1);
+            atomicOr(prm.status, kStatusTimeout);
         }
         {
             constexpr int NE_ = GG::P * NK * kCh;
@@ -528,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         // ---- the stage buffers must be free: MMAs of stage g - 2 complete ----
         if (gg >= 2 && !mbar_wait_bounded(&bar_mma[sb], ((gg >> 1) - 1) & 1, kWaitNs)) {
             *s_abort = 1;
-            atomicExch(prm.status, 1);
+            atomicOr(prm.status, kStatusTimeout);
         }
         __syncthreads();
 
@@ -698,7 +734,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
         // ---- epilogue of the job: V = acc_re + i acc_im, Sigma += sum_j V_j dH_j^+ ----
         if (!mbar_wait_bounded(bar_job, job_ctr & 1, kWaitNs)) {
             *s_abort = 1;
-            atomicExch(prm.status, 1);
+            atomicOr(prm.status, kStatusTimeout);
         }
         tc_fence_after();
         ++job_ctr;
@@ -763,7 +799,8 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                         }
                     }
                 }
-                if (ep_live) {
+                if (ep_live && SSE_BC((ep_dst[0] - S) + EP_S - 1, (long long)d.nkz * d.ne * d.na * kCh, prm.status) &&
+                    SSE_BC((ep_dst[1] - S) + EP_S - 1, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) {
 #pragma unroll
                     for (int rl = 0; rl < 2; ++rl)
 #pragma unroll
@@ -861,8 +898,9 @@ __host__ __device__ constexpr uint32_t tc_entry_bytes(int nw) { return tc_table_
 // i (Vi Hr - Vr Hi); every value split into bf16 hi + lo.
 template <typename CT>
 __global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restrict__ D, const CT *__restrict__ dH,
-                                                              const int32_t *__restrict__ neigh, uint8_t *__restrict__ out,
-                                                              int na, int nb, int nqz, int nw) {
+                                                              const int32_t *__restrict__ neigh,
+                                                              const int32_t *__restrict__ rev, uint8_t *__restrict__ out,
+                                                              int na, int nb, int nqz, int nw, int32_t *status) {
     constexpr int NK = 5;
     using GG = Geo<NK>;
     extern __shared__ __align__(16) uint8_t tsm[];
@@ -879,7 +917,7 @@ __global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restri
         const int ij = x % 9, w = (x / 9) % nw, kap = x / (9 * nw);
         float2 acc = make_float2(0.f, 0.f);
         for (int q = kap; q < nqz; q += NK) {
-            const float2 v = load_c32(D + ((((size_t)q * nw + w) * na + a) * nb + b) * 9 + ij);
+            const float2 v = load_dt(D, neigh, rev, q, w, nw, na, nb, a, b, ij, status);
             acc.x += v.x;
             acc.y += v.y;
         }
@@ -1100,11 +1138,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 for (int x = tid; x < NK * GG::TE * kCh; x += kTcThreads) {
                     const int e = x / (NK * kCh), k = (x / kCh) % NK, c = x % kCh;
                     const int E = t * GG::TE + e;
-                    if (E < d.ne) {
+                    const size_t idx = (((size_t)k * d.ne + E) * d.na + a) * kCh + c;
+                    if (E < d.ne && SSE_BC(idx, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) {
                         CT z;
                         z.x = 0;
                         z.y = 0;
-                        S[(((size_t)k * d.ne + E) * d.na + a) * kCh + c] = z;
+                        S[idx] = z;
                     }
                 }
         }
@@ -1245,7 +1284,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 }
                 if (!ok) {
                     *s_abort_ctl = 1;
-                    atomicExch(prm.status, 1);
+                    atomicOr(prm.status, kStatusTimeout);
                 }
             }
             __syncwarp();
@@ -1275,8 +1314,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             if (Ep >= 0 && Ep < d.ne) slice = (long long)Ep * d.na + f;
                         }
                         const uint8_t *sl = gws + slice * kXpSlice;
-                        bulk_g2s(dst + h * 4096, sl, 4096, &bar_g[slot]);
-                        bulk_g2s(dst + 8192 + h * 4096, sl + 4096, 4096, &bar_g[slot]);
+                        // a skipped copy leaves the pair's barrier short: its wait then times out
+                        if (SSE_BC(slice, (long long)d.ne * d.na + 1, prm.status)) {
+                            bulk_g2s(dst + h * 4096, sl, 4096, &bar_g[slot]);
+                            bulk_g2s(dst + 8192 + h * 4096, sl + 4096, 4096, &bar_g[slot]);
+                        }
                     }
                     last_g[slot] = pair_ctr++;
                     return true;
@@ -1294,7 +1336,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     // the small operands first: the pre-product can start while the table streams in
                     // (the failure-injection hook skips the tables of the CTA's first unit's second
                     // slot, its only slot if it has one)
-                    if (!(prm.inject && iter == 0 && vs == (nvalid > 1 ? 1 : 0))) {
+                    if (!(prm.inject && iter == 0 && vs == (nvalid > 1 ? 1 : 0)) &&
+                        SSE_BC((size_t)a * d.nb + s_slot[vs], (long long)d.na * d.nb, prm.status)) {
                         const uint8_t *src = I.sws[sign] + ((size_t)a * d.nb + s_slot[vs]) * ebytes;
                         mbar_arrive_expect_tx(bar_slot, 16384 + 2 * kPostBPlane);
                         bulk_g2s(sApre, src + tbytes, 16384, bar_slot);
@@ -1307,7 +1350,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 }
                 if (!ok) {
                     *s_abort_prd = 1;
-                    atomicExch(prm.status, 1);
+                    atomicOr(prm.status, kStatusTimeout);
                 }
             }
             __syncwarp();
@@ -1325,7 +1368,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             auto bwait = [&](uint64_t *bar, uint32_t parity) {
                 if (!bad && !mbar_wait_bounded_sleep(bar, parity, kWaitNs)) {
                     bad = true;
-                    atomicExch(prm.status, 1);
+                    atomicOr(prm.status, kStatusTimeout);
                 }
             };
             for (int g = 0; g < total; ++g, advance(cur), o = (o + 1 == slot_len) ? 0 : o + 1) {
@@ -1338,7 +1381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     constexpr int kLines = (kCh * (int)sizeof(CT) + 127) / 128;
                     for (int x = tid; x < NK * GG::TE * kLines; x += kTcBuilders) {
                         const int pt = x / kLines, ln = x % kLines, k = pt / GG::TE, E = E0 + pt % GG::TE;
-                        if (E < d.ne)
+                        if (E < d.ne && SSE_BC((((size_t)k * d.ne + E) * d.na + a) * kCh, (long long)d.nkz * d.ne * d.na * kCh, prm.status))
                             prefetch_l2((const uint8_t *)(S + (((size_t)k * d.ne + E) * d.na + a) * kCh) + ln * 128);
                     }
                 }
@@ -1493,7 +1536,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tmem_ld_wait();
                             tc_fence_before();
                         }
-                        if (q > 0 && dlive) {
+                        if (q > 0 && dlive && SSE_BC((dst - S) + 3, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) {
                             // the slot's FP32 contribution into Sigma: the first slot stores it, every
                             // later slot adds it with a fire-and-forget reduction at L2 (FP64 adds for
                             // complex128, the running sum then being FP64; FP32 adds for complex64)
@@ -1613,7 +1656,7 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
 // One instance descriptor from a plan and its buffers; the requested signs are packed
 // into slots 0 and 1.  Returns false when no sign is requested.
 template <int NK>
-bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc) {
+bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc, bool dfull) {
     using GG = Geo<NK>;
     const bool do_gt = io.S_gt != nullptr, do_lt = io.S_lt != nullptr;
     I.nsign = (int)do_gt + (int)do_lt;
@@ -1626,6 +1669,7 @@ bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc) {
     I.S[1] = io.S_lt;
     I.dH = p.geo.dH;
     I.neigh = p.geo.neigh;
+    I.rev = dfull ? p.d_rev : nullptr;
     I.na = p.d.na;
     I.ne = p.d.ne;
     I.nb = p.d.nb;
@@ -1671,7 +1715,7 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
 // Fill the plan's workspace for every requested sign of one instance: G re-encoded for the
 // pre-product and the slot tables.
 template <typename CT>
-sse_status split_g(const Plan &p, const sse_io &io, cudaStream_t st) {
+sse_status split_g(const Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
     const size_t sign_bytes = ((size_t)p.d.ne * p.d.na + 1) * 8192;
     const size_t tab_sign = (size_t)p.d.na * p.d.nb * tc_entry_bytes(p.d.nw);
     const void *gs[2] = {io.S_gt ? io.G_gt : nullptr, io.S_lt ? io.G_lt : nullptr};
@@ -1687,8 +1731,8 @@ sse_status split_g(const Plan &p, const sse_io &io, cudaStream_t st) {
         sse_split_g_kernel<CT><<<(unsigned)slices, 256, 0, st>>>((const CT *)gs[s], ws + s * sign_bytes, p.d.ne,
                                                                 p.d.na, p.d.nkz);
         sse_slot_tables_kernel<CT><<<(unsigned)(p.d.na * p.d.nb), 256, tsmem, st>>>(
-            (const CT *)ds[s], (const CT *)p.geo.dH, p.geo.neigh, ws + 2 * sign_bytes + s * tab_sign, p.d.na, p.d.nb,
-            p.d.nqz, p.d.nw);
+            (const CT *)ds[s], (const CT *)p.geo.dH, p.geo.neigh, dfull ? p.d_rev : nullptr,
+            ws + 2 * sign_bytes + s * tab_sign, p.d.na, p.d.nb, p.d.nqz, p.d.nw, p.d_status);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch the workspace kernels");
@@ -1700,7 +1744,7 @@ bool aligned16(const sse_io &io) {
 }
 
 template <int NK, typename CT, bool V3>
-sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
+sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
     using GG = Geo<NK>;
     MixParams prm{};
     uint32_t smem = 0;
@@ -1714,7 +1758,7 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     const long long per_chunk = (long long)((io.S_gt != nullptr) + (io.S_lt != nullptr)) * p.d.na;
     int tpc = ntiles;
     while (tpc > 1 && per_chunk * ((ntiles + tpc - 1) / tpc) < 8LL * sms) tpc = (tpc + 1) / 2;
-    if (!fill_inst<NK>(prm.inst[0], p, io, tpc)) return SSE_OK;
+    if (!fill_inst<NK>(prm.inst[0], p, io, tpc, dfull)) return SSE_OK;
     prm.n_inst = 1;
     prm.inject = take_inject(SSE_INJECT_STALL) ? 1 : 0;
     prm.inst[0].unit_begin = 0;
@@ -1724,7 +1768,7 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st) {
     const int ts = timing_slot(p);
     timing_mark(p, ts, 0, st);
     if (V3) {
-        rs = split_g<CT>(p, io, st);
+        rs = split_g<CT>(p, io, st, dfull);
         if (rs != SSE_OK) return rs;
     }
     timing_mark(p, ts, 1, st);
@@ -1756,9 +1800,9 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
             const Plan &p = *plans[order[x]];
             const sse_io &io = ios[order[x]];
             if (!aligned16(io)) return set_error("mixed mode: G buffers must be 16-byte aligned"), SSE_E_INVALID_ARG;
-            if (!fill_inst<NK>(prm.inst[m], p, io, tpc)) continue;
+            if (!fill_inst<NK>(prm.inst[m], p, io, tpc, false)) continue;
             if (V3) {
-                rs = split_g<CT>(p, io, st);
+                rs = split_g<CT>(p, io, st, false);
                 if (rs != SSE_OK) return rs;
             }
             prm.inst[m].unit_begin = units;
@@ -1784,13 +1828,14 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
 }
 
 template <typename CT>
-sse_status launch_dtype(Plan &p, const sse_io &io, cudaStream_t st) {
+sse_status launch_dtype(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
     switch (p.d.nkz) {
-        case 1: return launch_nk<1, CT, false>(p, io, st);
-        case 2: return launch_nk<2, CT, false>(p, io, st);
-        case 3: return launch_nk<3, CT, false>(p, io, st);
-        case 4: return launch_nk<4, CT, false>(p, io, st);
-        case 5: return p.mixed_ws ? launch_nk<5, CT, true>(p, io, st) : launch_nk<5, CT, false>(p, io, st);
+        case 1: return launch_nk<1, CT, false>(p, io, st, dfull);
+        case 2: return launch_nk<2, CT, false>(p, io, st, dfull);
+        case 3: return launch_nk<3, CT, false>(p, io, st, dfull);
+        case 4: return launch_nk<4, CT, false>(p, io, st, dfull);
+        case 5:
+            return p.mixed_ws ? launch_nk<5, CT, true>(p, io, st, dfull) : launch_nk<5, CT, false>(p, io, st, dfull);
         default:
             set_error("mixed mode supports Nkz <= 5 (got %d)", p.d.nkz);
             return SSE_E_INVALID_ARG;
@@ -1883,9 +1928,9 @@ void mixed_plan_free(Plan &p) {
     p.mixed_ws_bytes = 0;
 }
 
-sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st) {
-    if (p.geo.dtype == SSE_C128) return launch_dtype<double2>(p, io, st);
-    return launch_dtype<float2>(p, io, st);
+sse_status launch_mixed(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
+    if (p.geo.dtype == SSE_C128) return launch_dtype<double2>(p, io, st, dfull);
+    return launch_dtype<float2>(p, io, st, dfull);
 }
 
 sse_status launch_mixed_batch(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,

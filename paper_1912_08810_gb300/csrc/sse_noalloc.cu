@@ -133,6 +133,7 @@ extern "C" SSE_API sse_status sse_execute_noalloc(const sse_geometry *geo, const
     e = cudaMemcpyAsync(words, scratch, sizeof words, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "synchronise sse_execute_noalloc");
+    if (words[2] & kStatusBounds) return set_error("a kernel computed an index outside one of its buffers"), SSE_E_BOUNDS;
     if (words[2] != 0) return set_error("a device-side wait of the mixed kernel expired"), SSE_E_TIMEOUT;
     return SSE_OK;
 }

@@ -212,6 +212,7 @@ void server_loop(sse_server_s *s) {
             }
             sse_status st = SSE_OK;
             if (e != cudaSuccess) st = cuda_fail(e, "round");
+            else if (*slot.h_status & kStatusBounds) st = SSE_E_BOUNDS;
             else if (*slot.h_status != 0) st = SSE_E_TIMEOUT;
             finish_round(s, s->running[i], st);
             s->running.erase(s->running.begin() + (long)i);

@@ -268,3 +268,32 @@ def make_batched_torch(spec: BatchedSpec, seed: int, *, device="cuda", which: Op
         inst["geometry"] = g
         out.append(inst)
     return out
+
+
+def make_phonon_full(geo: Geometry, seed: int, neigh: np.ndarray, *, dtype=np.complex128) -> Dict[str, np.ndarray]:
+    """Full phonon tensors D^>, D^< [nqz][nw][na][nb+1][3][3] (Section 2's shape: block nb of
+    an atom is its diagonal block), complex normal, with the structure of a Hermitian
+    matrix in (atom, direction): diagonal blocks B + B^dagger, and for each bond listed in
+    both directions the reverse block the conjugate transpose of the forward one.  Draw
+    order from default_rng(seed): D^> then D^<."""
+    rng = np.random.default_rng(seed)
+    neigh = np.ascontiguousarray(neigh, dtype=np.int32)
+    na, nb = neigh.shape
+    out = {}
+    for name in ("D_gt_full", "D_lt_full"):
+        d = _complex_normal(rng, (geo.nqz, geo.nw, na, nb + 1, N3D, N3D))
+        d[:, :, :, nb] = d[:, :, :, nb] + np.conj(np.swapaxes(d[:, :, :, nb], -1, -2))
+        done = set()
+        for a in range(na):
+            for s in range(nb):
+                b = int(neigh[a, s])
+                if b < 0 or (a, s) in done:
+                    continue
+                rev = [t for t in range(nb) if int(neigh[b, t]) == a and (b, t) not in done]
+                if not rev or b == a:
+                    continue
+                d[:, :, b, rev[0]] = np.conj(np.swapaxes(d[:, :, a, s], -1, -2))
+                done.add((a, s))
+                done.add((b, rev[0]))
+        out[name] = np.ascontiguousarray(d, dtype=dtype)
+    return out

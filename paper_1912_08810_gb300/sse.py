@@ -27,6 +27,7 @@ SSE_E_TIMEOUT = -5
 SSE_E_UNKNOWN_TICKET = -6
 SSE_E_SHUTDOWN = -7
 SSE_E_CANCELLED = -9
+SSE_E_BOUNDS = -10
 
 SSE_C128 = 0
 SSE_C64 = 1
@@ -44,6 +45,7 @@ EXPORTED = (
     "sse_execute_noalloc", "sse_execute_batch", "sse_batch_tuning",
     "sse_server_create", "sse_submit", "sse_poll", "sse_server_shutdown", "sse_server_destroy",
     "sse_server_stats", "sse_plan_set_timing", "sse_plan_timing", "sse_debug_inject",
+    "sse_dtilde", "sse_retarded", "sse_execute_full", "sse_pi",
 )
 
 
@@ -84,12 +86,13 @@ _lib = None
 
 
 def load(path: Optional[str] = None):
-    """Load the CUDA library once; raises if it has not been built."""
+    """Load the CUDA library once; raises if it has not been built.  SSE_GB300_LIB may name
+    another build of it (the bounds-checked libsse_gb300_bc.so)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        p = path or os.environ.get("SSE_GB300_LIB") or LIB_PATH
         if not os.path.exists(p):
             raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
         lib = ctypes.CDLL(p)
@@ -114,6 +117,10 @@ def load(path: Optional[str] = None):
             "sse_server_shutdown": ([vp], st),
             "sse_server_destroy": ([vp], st),
             "sse_debug_inject": ([st], st),
+            "sse_dtilde": ([vp, vp, vp, vp], st),
+            "sse_retarded": ([vp, vp, vp, vp, vp], st),
+            "sse_execute_full": ([vp, ctypes.POINTER(sse_io), vp, vp], st),
+            "sse_pi": ([vp, vp, vp, vp, vp, vp], st),
             "sse_server_stats": ([vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                   ctypes.POINTER(ctypes.c_int32)], st),
             "sse_plan_set_timing": ([vp, ctypes.c_int32], st),
@@ -181,6 +188,29 @@ def sse_plan_timing(plan):
     a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
     _check(load().sse_plan_timing(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)), "sse_plan_timing")
     return a.value, b.value, n.value
+
+
+def sse_dtilde(plan, D: int, Dt: int, stream: int = 0) -> None:
+    """Pre-combined phonon term of Eq. 3 (device pointers; see include/sse.h)."""
+    _check(load().sse_dtilde(plan, ctypes.c_void_p(D), ctypes.c_void_p(Dt), ctypes.c_void_p(stream)), "sse_dtilde")
+
+
+def sse_retarded(plan, S_gt: int, S_lt: int, S_r: int, stream: int = 0) -> None:
+    """Sigma^R = (Sigma^> - Sigma^<) / 2 (device pointers)."""
+    _check(load().sse_retarded(plan, ctypes.c_void_p(S_gt), ctypes.c_void_p(S_lt), ctypes.c_void_p(S_r),
+                               ctypes.c_void_p(stream)), "sse_retarded")
+
+
+def sse_execute_full(plan, io: sse_io, S_r: Optional[int] = None, stream: int = 0) -> None:
+    """Full phonon tensors in io.D_gt / io.D_lt; Sigma^> / Sigma^< and optionally Sigma^R out."""
+    _check(load().sse_execute_full(plan, ctypes.byref(io), ctypes.c_void_p(S_r), ctypes.c_void_p(stream)),
+           "sse_execute_full")
+
+
+def sse_pi(plan, G_gt: int, G_lt: int, Pi_gt: Optional[int], Pi_lt: Optional[int], stream: int = 0) -> None:
+    """Phonon self-energy of Eqs. 4-5 (device pointers; see include/sse.h)."""
+    _check(load().sse_pi(plan, ctypes.c_void_p(G_gt), ctypes.c_void_p(G_lt), ctypes.c_void_p(Pi_gt),
+                         ctypes.c_void_p(Pi_lt), ctypes.c_void_p(stream)), "sse_pi")
 
 
 def sse_execute_noalloc(geo: sse_geometry, io: sse_io, stream: int = 0) -> None:
@@ -325,6 +355,53 @@ class Plan:
                 raise ValueError("execute_host() takes host tensors")
         s = stream if stream is not None else torch.cuda.current_stream()
         sse_execute_host(self.handle, self._io(G_gt, G_lt, D_gt, D_lt, S_gt, S_lt), s.cuda_stream)
+
+    def dtilde(self, D, Dt, stream=None) -> None:
+        """Dt [nqz, nw, na, nb, 3, 3] from the full phonon tensor D [nqz, nw, na, nb + 1, 3, 3]."""
+        import torch
+        nqz, nw, na, nb = self.shape_d[:4]
+        self._check_tensor(D, (nqz, nw, na, nb + 1, 3, 3))
+        self._check_tensor(Dt, self.shape_d)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sse_dtilde(self.handle, _ptr(D), _ptr(Dt), s.cuda_stream)
+
+    def retarded(self, S_gt, S_lt, S_r, stream=None) -> None:
+        import torch
+        for t in (S_gt, S_lt, S_r):
+            self._check_tensor(t, self.shape_g)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sse_retarded(self.handle, _ptr(S_gt), _ptr(S_lt), _ptr(S_r), s.cuda_stream)
+
+    def execute_full(self, G_gt=None, G_lt=None, D_gt=None, D_lt=None, S_gt=None, S_lt=None, S_r=None,
+                     stream=None) -> None:
+        """As execute(), with the FULL phonon tensors [nqz, nw, na, nb + 1, 3, 3] in D_gt / D_lt;
+        also writes Sigma^R into S_r when given."""
+        import torch
+        nqz, nw, na, nb = self.shape_d[:4]
+        full = (nqz, nw, na, nb + 1, 3, 3)
+        for t, shp in ((G_gt, self.shape_g), (G_lt, self.shape_g), (S_gt, self.shape_g), (S_lt, self.shape_g),
+                       (S_r, self.shape_g), (D_gt, full), (D_lt, full)):
+            if t is not None:
+                self._check_tensor(t, shp)
+        io = sse_io(_ptr(G_gt), _ptr(G_lt), _ptr(D_gt), _ptr(D_lt), _ptr(S_gt), _ptr(S_lt))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sse_execute_full(self.handle, io, _ptr(S_r), s.cuda_stream)
+
+    def pi(self, G_gt, G_lt, Pi_gt=None, Pi_lt=None, stream=None) -> None:
+        """Pi^> / Pi^< [nqz, nw, na, nb + 1, 3, 3] from G^> and G^< (both needed for either sign)."""
+        import torch
+        nqz, nw, na, nb = self.shape_d[:4]
+        for t, shp in ((G_gt, self.shape_g), (G_lt, self.shape_g), (Pi_gt, (nqz, nw, na, nb + 1, 3, 3)),
+                       (Pi_lt, (nqz, nw, na, nb + 1, 3, 3))):
+            if t is not None:
+                self._check_tensor(t, shp)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sse_pi(self.handle, _ptr(G_gt), _ptr(G_lt), _ptr(Pi_gt), _ptr(Pi_lt), s.cuda_stream)
+
+    def _check_tensor(self, t, shp) -> None:
+        if not t.is_cuda or tuple(t.shape) != tuple(shp) or t.dtype != self.torch_dtype or not t.is_contiguous():
+            raise ValueError(f"tensor mismatch: shape {tuple(t.shape)} dtype {t.dtype}; want {tuple(shp)} "
+                             f"{self.torch_dtype}, contiguous, on the GPU")
 
     def status(self) -> None:
         sse_plan_status(self.handle)

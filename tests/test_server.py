@@ -85,6 +85,7 @@ def test_budget_limits_admission_and_errors_are_codes():
     for r in reqs:
         g = r["inst"]["geometry"]
         nb = (2 * g.nkz * g.ne * g.na * 144 + g.nqz * g.nw * g.na * g.nb * 9) * 8 * 2
+        nb += r["plan"].info().workspace_bytes  # admission also counts what the plan holds
         one = nb if one is None else max(one, nb)
     # a budget for one request at a time: every round holds exactly one request
     server = sse.sse_server_create(one, 8, 5000)
@@ -110,8 +111,11 @@ def test_budget_limits_admission_and_errors_are_codes():
 def test_destroy_with_pending_work_returns():
     reqs = make_requests(6, 23)
     server = sse.sse_server_create(1 << 40, 1, 10000)
-    for r in reqs:
-        sse.sse_submit(server, r["plan"].handle, r["io"])
+    tickets = [sse.sse_submit(server, r["plan"].handle, r["io"]) for r in reqs]
     t0 = time.time()
-    sse.sse_server_destroy(server)  # cancels what has not started, drains the rest
+    sse.sse_server_shutdown(server)  # cancels what has not started, drains the rest
+    codes = [sse.sse_poll(server, t)[0] for t in tickets]
+    sse.sse_server_destroy(server)
     assert time.time() - t0 < 10.0
+    assert all(c in (sse.SSE_OK, sse.SSE_E_CANCELLED) for c in codes)
+    assert sse.SSE_E_CANCELLED in codes  # one admitted at a time: not all six ran
