@@ -20,7 +20,9 @@
  *    forward block dH[a,slot,j] (the listing's float64 dH is taken complex);
  *  - kz - qz wraps modulo Nkz (kz is periodic on [-pi, pi], Section 2);
  *  - the phonon frequency index w means (w + omega_first) energy-grid steps, and an
- *    energy E - omega below the grid contributes nothing (no wrap);
+ *    energy E - omega off the grid contributes nothing (no wrap); omega_first may be
+ *    negative, so one frequency grid can hold both E - hbar omega and E + hbar omega (the
+ *    two-sided exchange G(E +- hbar omega) of Section 3, "Communication Avoidance");
  *  - Dt is the already pre-combined D_ba - D_bb - D_aa + D_ab (Section 3 input list);
  *  - Sigma is overwritten (accumulated into zero, the SCBA start value of Section 2).
  *
@@ -92,7 +94,7 @@ static void matmul_adj(int n, const cplx *a, const cplx *b, cplx *c) {
 
 static int valid_geometry(const oracle_geometry *g) {
     return g && g->nkz > 0 && g->nqz > 0 && g->ne > 0 && g->nw > 0 && g->na > 0 &&
-           g->nb > 0 && g->norb > 0 && g->omega_first >= 0;
+           g->nb > 0 && g->norb > 0 && g->omega_first > -(1 << 20) && g->omega_first < (1 << 20);
 }
 
 static int wrap_k(int k, int q, int nkz) {
@@ -133,7 +135,7 @@ int oracle_sigma_points(const oracle_geometry *g, const int32_t *neigh, const cp
                     for (int q = 0; q < g->nqz; ++q)
                         for (int w = 0; w < g->nw; ++w) {
                             const int ep = e - (w + g->omega_first);
-                            if (ep < 0) continue; /* E - omega below the energy grid */
+                            if (ep < 0 || ep >= g->ne) continue; /* E - omega off the energy grid */
                             const cplx d = Dt[d_index(g, q, w, a, slot, i, j)];
                             const cplx *gb = G + g_index(g, wrap_k(k, q, g->nkz), ep, f);
                             matmul(n, dH + dh_index(g, a, slot, i), gb, x);   /* dH_i . G       */
@@ -191,7 +193,7 @@ int oracle_sigma_atoms(const oracle_geometry *g, const int32_t *neigh, const cpl
                             for (int q = 0; q < g->nqz; ++q)
                                 for (int w = 0; w < g->nw; ++w) {
                                     const int ep = e - (w + g->omega_first);
-                                    if (ep < 0) continue;
+                                    if (ep < 0 || ep >= g->ne) continue;
                                     const cplx d = Dt[d_index(g, q, w, a, slot, i, j)];
                                     const cplx *m = M + ((((size_t)wrap_k(k, q, g->nkz) * g->ne + ep) * N3D + i) * N3D + j) * nn;
                                     for (int r = 0; r < nn; ++r) acc[r] += d * m[r];
@@ -313,7 +315,7 @@ int oracle_pi(const oracle_geometry *g, const int32_t *neigh, const cplx *dH, co
                                 for (int k = 0; k < g->nkz; ++k)
                                     for (int e = 0; e < g->ne; ++e) {
                                         const int ep = e + w + g->omega_first;
-                                        if (ep >= g->ne) continue; /* E + omega above the energy grid */
+                                        if (ep < 0 || ep >= g->ne) continue; /* E + omega off the energy grid */
                                         const int kq = (k + q) % g->nkz;
                                         matmul(n, hi, Ga + g_index(g, kq, ep, a), x);  /* dH_i^+ . Ga      */
                                         matmul(n, x, hJ, y);                            /* ... . dH_j       */

@@ -41,7 +41,7 @@ def test_scalar_correlation_matches_numpy():
     """Norb = 1, Nkz = 1, dH = 1: Pi(w) = sum_E Ga[E + omega_w] Gb[E], a cross-correlation."""
     rng = np.random.default_rng(1)
     ne, nw = 17, 6
-    for of in (0, 1, 3):
+    for of in (0, 1, 3, -2, -5):  # negative: E - |omega| as well (two-sided grid)
         x = rng.standard_normal(ne) + 1j * rng.standard_normal(ne)
         y = rng.standard_normal(ne) + 1j * rng.standard_normal(ne)
         Ga = np.zeros((1, ne, 2, 1, 1), complex)
@@ -53,7 +53,7 @@ def test_scalar_correlation_matches_numpy():
         c = np.correlate(x, np.conj(y), mode="full")  # c[lag + ne - 1] = sum_n x[n + lag] y[n]
         for w in range(nw):
             lag = w + of
-            want = c[lag + ne - 1] if lag < ne else 0
+            want = c[lag + ne - 1] if -ne < lag < ne else 0
             assert Pi[0, w, 0, 0, 0, 0] == pytest.approx(want, abs=1e-12)
 
 

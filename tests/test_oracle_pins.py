@@ -96,7 +96,7 @@ def physics_form(inst, sign="gt", omega_first=1):
             for q in range(nqz):
                 for w in range(nw):
                     ep = e - (w + omega_first)
-                    if ep < 0:
+                    if ep < 0 or ep >= ne:
                         continue
                     Gd = np.zeros((N, N), complex)
                     for b in range(na):
@@ -138,8 +138,11 @@ def test_nqz_differs_from_nkz():
     assert rel(full, ref) < 1e-13 and rel(pp, ref) < 1e-13
 
 
-def test_omega_first_zero_and_two():
-    for of in (0, 2):
+def test_omega_first_zero_two_and_two_sided():
+    """omega_first = 0 and 2, and negative omega_first: a frequency grid spanning both signs,
+    so Sigma(E) gathers G(E - hbar omega) and G(E + hbar omega) (the two-sided exchange of
+    Section 3, "Communication Avoidance")."""
+    for of in (0, 2, -2, -4):
         inst = small_instance(nkz=2, nqz=2, ne=6, nw=3, na=4, nb=2, norb=2, seed=9 + of)
         ref = physics_form(inst, omega_first=of)
         full, pp = both(inst, omega_first=of)
@@ -209,6 +212,26 @@ def test_scalar_correlation_matches_convolve():
                 expect[k] += np.convolve(Gq[k], filt)[:ne]
         expect *= abs(dH[a, 0, 0, 0, 0]) ** 2
         assert rel(S[:, :, a, 0, 0], expect) < 1e-13
+
+
+def test_two_sided_scalar_case_matches_convolve():
+    """Norb = 1, Nkz = Nqz = 1, frequencies omega_w = w + omega_first from -m to nw - 1 - m:
+    Sigma[E] = sum_w Dt[w] G[E - omega_w], a full convolution read m samples later."""
+    rng = np.random.default_rng(8)
+    ne, nw = 15, 7
+    neigh = np.array([[0]], dtype=np.int32)
+    G = rng.standard_normal((1, ne, 1, 1, 1)) + 1j * rng.standard_normal((1, ne, 1, 1, 1))
+    dH = np.ones((1, 1, 3, 1, 1), complex)
+    D = np.zeros((1, nw, 1, 1, 3, 3), complex)
+    D[0, :, 0, 0, 0, 0] = rng.standard_normal(nw) + 1j * rng.standard_normal(nw)
+    for m in (1, 3, 6, 9):
+        S = oracle.sigma_atoms(G, D, dH, neigh, omega_first=-m)
+        full = np.convolve(G[0, :, 0, 0, 0], D[0, :, 0, 0, 0, 0])
+        expect = np.zeros(ne, complex)
+        for e in range(ne):
+            if 0 <= e + m < full.size:
+                expect[e] = full[e + m]
+        assert rel(S[0, :, 0, 0, 0], expect) < 1e-13, m
 
 
 # --- linearity, zero and delta Dt ---------------------------------------------------------------
