@@ -14,7 +14,7 @@
  *   - the prefactor i and the frequency weight of Eq. 3 are the caller's (factor 1);
  *   - the sum index l of Eq. 3 is the neighbour slot;
  *   - grad_j H_ba is the conjugate transpose of the stored dH[a,slot,j];
- *   - kz - qz wraps modulo nkz; E - omega below the grid contributes 0;
+ *   - kz - qz wraps modulo nkz; E - omega off the energy grid contributes 0;
  *   - Sigma is overwritten, not accumulated.
  *
  * Layouts (row-major; complex = interleaved re/im, double2 for SSE_C128, float2 for
@@ -80,7 +80,8 @@ typedef enum { SSE_MODE_FP64 = 0, SSE_MODE_MIXED = 1 } sse_mode;
 typedef struct {
     int32_t nkz, nqz, ne, nw, na, nb_max;
     int32_t norb;         /* must be 12 */
-    int32_t omega_first;  /* w means (w + omega_first) energy-grid steps; >= 0 */
+    int32_t omega_first;  /* w means (w + omega_first) energy-grid steps; may be negative: a grid
+                             spanning both signs gives the two-sided exchange E -+ hbar omega */
     const int32_t *neigh; /* device [na][nb_max] */
     const void *dH;       /* device [na][nb_max][3][12][12] */
     int32_t dtype;        /* sse_dtype */

@@ -39,9 +39,10 @@ sse_status cuda_fail(cudaError_t e, const char *what) {
 double algorithmic_cmacs(const Dims &d, const std::vector<int32_t> &neigh) {
     int64_t bonds = 0;
     for (int32_t f : neigh) bonds += f >= 0;
-    int64_t valid_w = 0;  // sum_w max(0, ne - (w + omega_first))
+    int64_t valid_w = 0;  // sum_w max(0, ne - |w + omega_first|): E and E - omega both on the grid
     for (int w = 0; w < d.nw; ++w) {
-        const int64_t v = (int64_t)d.ne - (w + d.omega_first);
+        const int64_t om = (int64_t)w + d.omega_first;
+        const int64_t v = (int64_t)d.ne - (om < 0 ? -om : om);
         valid_w += v > 0 ? v : 0;
     }
     const double products = (double)bonds * d.nkz * d.ne * 12.0 * kNorb * kNorb * kNorb;  // M_ij once per (k', E')
@@ -69,7 +70,8 @@ static sse_status check_geometry(const sse_geometry *g) {
         return SSE_E_INVALID_ARG;
     }
     if (g->norb != kNorb) return set_error("norb must be 12 (got %d)", g->norb), SSE_E_INVALID_ARG;
-    if (g->omega_first < 0) return set_error("omega_first must be >= 0"), SSE_E_INVALID_ARG;
+    if (g->omega_first <= -(1 << 20) || g->omega_first >= (1 << 20))
+        return set_error("omega_first out of range"), SSE_E_INVALID_ARG;
     if (g->dtype != SSE_C128 && g->dtype != SSE_C64) return set_error("unknown dtype %d", g->dtype), SSE_E_INVALID_ARG;
     if (g->mode != SSE_MODE_FP64 && g->mode != SSE_MODE_MIXED)
         return set_error("unknown mode %d", g->mode), SSE_E_INVALID_ARG;

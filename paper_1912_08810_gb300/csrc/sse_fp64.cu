@@ -96,7 +96,8 @@ sse_fp64_direct_kernel(const int32_t *__restrict__ neigh, const CT *__restrict__
                 const CT *dq = D + (((size_t)q * d.nw) * d.na + a) * d.nb * 9 + (size_t)slot * 9;
                 for (int w = 0; w < d.nw; ++w) {
                     const int ep = e - w - d.omega_first;
-                    if (ep < 0) break;  // every later w is further below the grid
+                    if (ep < 0) break;         // every later w is further below the grid
+                    if (ep >= d.ne) continue;  // E + |omega| above the grid (negative omega_first)
                     const CT *gp = gq + (size_t)ep * d.na * kBlk;
                     const CT *dw = dq + (size_t)w * d.na * d.nb * 9;
                     if (!SSE_BC(gp - G, (long long)d.nkz * d.ne * d.na * kBlk, status) ||

@@ -88,7 +88,7 @@ extern "C" SSE_API sse_status sse_execute_noalloc(const sse_geometry *geo, const
     if (!geo || !io) return set_error("geometry or io is NULL"), SSE_E_INVALID_ARG;
     if (geo->mode != SSE_MODE_MIXED) return set_error("sse_execute_noalloc runs the mixed mode only"), SSE_E_INVALID_ARG;
     if (geo->nkz <= 0 || geo->nqz <= 0 || geo->ne <= 0 || geo->nw <= 0 || geo->na <= 0 || geo->nb_max <= 0 ||
-        geo->norb != kNorb || geo->omega_first < 0 || (geo->dtype != SSE_C128 && geo->dtype != SSE_C64) ||
+        geo->norb != kNorb || geo->omega_first <= -(1 << 20) || geo->omega_first >= (1 << 20) || (geo->dtype != SSE_C128 && geo->dtype != SSE_C64) ||
         !geo->neigh || !geo->dH)
         return set_error("invalid geometry for sse_execute_noalloc"), SSE_E_INVALID_ARG;
     if (geo->nkz > 5 || geo->nb_max > 32)

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kPiThreads, 2) sse_pi_kernel(const __grid_cons
                         __syncthreads();
                         if (E < 0 || !worker) continue;
                         const int epw = E + p.omega_first + w;  // this thread's V row
-                        if (epw >= p.ne) continue;              // E + omega above the grid
+                        if (epw < 0 || epw >= p.ne) continue;   // E + omega off the grid
                         const double2 *vr = s_ring + (size_t)(epw % nw) * 3 * kChunk;
                         for (int c = csub * per; c < (csub + 1) * per; ++c) {
                             double2 vi[3], uj[3];

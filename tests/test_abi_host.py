@@ -54,7 +54,7 @@ def test_null_arguments_are_rejected(lib):
 
 @pytest.mark.parametrize("field,value,msg", [
     ("nkz", 0, "positive"), ("ne", -3, "positive"), ("norb", 10, "norb"),
-    ("omega_first", -1, "omega_first"), ("dtype", 7, "dtype"), ("mode", 5, "mode"),
+    ("omega_first", -(1 << 20), "omega_first"), ("dtype", 7, "dtype"), ("mode", 5, "mode"),
 ])
 def test_bad_geometry_rejected_before_any_device_call(lib, field, value, msg):
     g = sse.sse_geometry(3, 3, 8, 2, 4, 2, 12, 1, None, None, 0, 0)

@@ -35,6 +35,7 @@ def test_tiny_config_both_signs():
     dict(nkz=4, nqz=2, ne=9, nw=6, na=5, nb=2, omega_first=0),    # omega_first = 0
     dict(nkz=2, nqz=2, ne=3, nw=8, na=6, nb=2, omega_first=2),    # most E - omega below the grid
     dict(nkz=1, nqz=1, ne=33, nw=5, na=1, nb=4, omega_first=1),   # one atom, one k
+    dict(nkz=3, nqz=3, ne=21, nw=9, na=6, nb=3, omega_first=-4),  # two-sided grid: E -+ omega
 ])
 def test_edge_geometries(case):
     of = case.pop("omega_first")

@@ -50,6 +50,9 @@ def test_every_supported_nkz(nkz):
     dict(nkz=5, nqz=5, ne=17, nw=32, na=3, nb=4, omega_first=1),  # Nw = 32 with a short grid
     dict(nkz=5, nqz=5, ne=21, nw=50, na=2, nb=2, omega_first=1),  # largest Nw of the warp-specialised form
     dict(nkz=5, nqz=5, ne=21, nw=56, na=2, nb=2, omega_first=1),  # past it: the single-role form takes over
+    dict(nkz=3, nqz=3, ne=37, nw=17, na=5, nb=3, omega_first=-8),  # two-sided grid, single-role form
+    dict(nkz=5, nqz=5, ne=30, nw=33, na=4, nb=3, omega_first=-16), # two-sided grid, warp-specialised form
+    dict(nkz=5, nqz=5, ne=12, nw=9, na=3, nb=2, omega_first=-12),  # all frequencies negative
 ])
 def test_edge_geometries(case):
     of = case.pop("omega_first")

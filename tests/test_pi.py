@@ -40,6 +40,7 @@ def ref_pi(inst, sign, nqz, nw, omega_first=1):
     dict(nkz=2, nqz=3, ne=9, nw=11, na=5, nb=2, of=2, dtype=np.complex128, chain=False),  # Nqz > Nkz, most E + w off the grid
     dict(nkz=3, nqz=3, ne=25, nw=16, na=8, nb=8, of=1, dtype=np.complex64, chain=False),  # batched-like, complex64
     dict(nkz=1, nqz=1, ne=30, nw=1, na=4, nb=4, of=1, dtype=np.complex128, chain=False),  # Nw = 1
+    dict(nkz=3, nqz=3, ne=18, nw=9, na=5, nb=3, of=-4, dtype=np.complex128, chain=False),  # two-sided grid
 ])
 def test_pi_matches_oracle(case):
     geo = inputs.Geometry(nkz=case["nkz"], nqz=case["nqz"], ne=case["ne"], nw=case["nw"], na=case["na"],
