@@ -55,9 +55,11 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", choices=("auto", "mixed", "fp64"), default="auto")
-    ap.add_argument("--workload", choices=("medium", "medium64", "tiny"), default="medium",
+    ap.add_argument("--workload", choices=("medium", "medium64", "tiny", "batched1"), default="medium",
                     help="medium: the benchmark workload; medium64: the same shape with Na=64 "
-                         "(small case for profiling); tiny: the smallest workload")
+                         "(small case for profiling); tiny: the smallest workload; batched1: one "
+                         "instance of the batched shape (Na=512, NE=256, Nkz=Nqz=3, Nw=16, 3..8 random "
+                         "neighbours, complex64), for profiling the form the batched and served runs use")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3,
@@ -73,16 +75,32 @@ def parse_args():
     return ap.parse_args()
 
 
+BATCHED1_SPEC = dict(n_instances=1, na_range=(512, 512), ne_range=(256, 256))
+
+
 def workload(name):
     from paper_1912_08810_gb300 import inputs
     small = inputs.Geometry(nkz=5, nqz=5, ne=256, nw=32, na=64, nb=4)
-    return {"medium": (inputs.MEDIUM, 1), "medium64": (small, 1), "tiny": (inputs.TINY, 0)}[name]
+    one = inputs.Geometry(nkz=3, nqz=3, ne=256, nw=16, na=512, nb=8)
+    return {"medium": (inputs.MEDIUM, 1), "medium64": (small, 1), "tiny": (inputs.TINY, 0),
+            "batched1": (one, 3)}[name]
+
+
+def make_workload(name):
+    from paper_1912_08810_gb300 import inputs
+    geo, seed = workload(name)
+    if name == "batched1":
+        return geo, inputs.make_batched(inputs.BatchedSpec(**BATCHED1_SPEC), seed)[0]
+    return geo, inputs.make_instance(geo, seed)
 
 
 def config_dict(geo, name, form):
-    in_bytes = 16 * (2 * geo.nkz * geo.ne * geo.na * 144 + 2 * geo.nqz * geo.nw * geo.na * geo.nb * 9)
+    eb = 8 if name == "batched1" else 16
+    in_bytes = eb * (2 * geo.nkz * geo.ne * geo.na * 144 + 2 * geo.nqz * geo.nw * geo.na * geo.nb * 9)
+    nbr = "3..8 random" if name == "batched1" else "chain"
+    dt = "complex64" if name == "batched1" else "complex128"
     return {"workload": f"{name} SSE: Nkz=Nqz={geo.nkz}, NE={geo.ne}, Nw={geo.nw}, Na={geo.na}, "
-                        f"Nb={geo.nb} chain, Norb=12, complex128",
+                        f"Nb={geo.nb} {nbr}, Norb=12, {dt}",
             "form": form, "nkz": geo.nkz, "nqz": geo.nqz, "ne": geo.ne, "nw": geo.nw, "na": geo.na,
             "nb": geo.nb, "norb": 12, "seed": workload(name)[1],
             "l2": f"inputs {in_bytes / 1e9:.2f} GB > 129 MB L2, no flush", "parallelism": "replicas"}
@@ -170,6 +188,8 @@ def profiled_traffic(kernel_tag, digest):
 KERNEL_SOURCES = {
     "fp64": ("sse_fp64_direct", ["paper_1912_08810_gb300/csrc/sse_fp64.cu"]),
     "mixed": ("sse_tc_kernel", ["paper_1912_08810_gb300/csrc/sse_mixed.cu", "paper_1912_08810_gb300/csrc/tc_ptx.h"]),
+    "mixed_single_role": ("sse_mixed_kernel", ["paper_1912_08810_gb300/csrc/sse_mixed.cu",
+                                               "paper_1912_08810_gb300/csrc/tc_ptx.h"]),
 }
 
 
@@ -314,8 +334,7 @@ def run_ours(args):
 
     world, rank, local = dist_setup(args)
     name = args.workload
-    geo, seed = workload(name)
-    inst = inputs.make_instance(geo, seed)
+    geo, inst = make_workload(name)
     dev = {k: torch.from_numpy(inst[k]).cuda().contiguous() for k in ("G_gt", "G_lt", "D_gt", "D_lt", "dH", "neigh")}
     S = {s: torch.empty_like(dev["G_gt"]) for s in ("gt", "lt")}
     stream = torch.cuda.current_stream()
@@ -354,11 +373,12 @@ def run_ours(args):
     value = whole_job_value(points, args.steps, world, total_ms_max)
     # our kernels per step: the workspace pass (re-encoded G and slot tables, per sign) of
     # the Nkz = 5 tensor-core form, then the main kernel
-    launches_per_step = 1 + (4 if (form == "mixed" and info.workspace_bytes > 1024) else 0)
+    launches_per_step = 1 + (4 if (form == "mixed" and info.workspace_bytes > (1 << 20)) else 0)
     kern_ms = main_ms / timed_calls if timed_calls else statistics.mean(per_step)
 
     peaks = load_peaks()
-    tag, srcs = KERNEL_SOURCES[form]
+    ws_form = form == "mixed" and info.workspace_bytes > (1 << 20)  # the warp-specialised form's workspace
+    tag, srcs = KERNEL_SOURCES["mixed" if ws_form else ("mixed_single_role" if form == "mixed" else form)]
     digest = source_digest(srcs)
     traffic = profiled_traffic(tag, digest)
     if form == "mixed":
@@ -667,8 +687,7 @@ def run_reference(args):
     import oracle
     from paper_1912_08810_gb300 import inputs
     name = args.workload
-    geo, seed = workload(name)
-    inst = inputs.make_instance(geo, seed)
+    geo, inst = make_workload(name)
     cores = oracle.num_threads()
     n = max(4, cores)
 
