@@ -24,6 +24,7 @@
 // job, drain the accumulators and apply dH_j^dagger.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stdlib.h>
 
 #include "sse_internal.h"
 #include "tc_ptx.h"
@@ -1758,6 +1759,10 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
     const long long per_chunk = (long long)((io.S_gt != nullptr) + (io.S_lt != nullptr)) * p.d.na;
     int tpc = ntiles;
     while (tpc > 1 && per_chunk * ((ntiles + tpc - 1) / tpc) < 8LL * sms) tpc = (tpc + 1) / 2;
+    // SSE_TILES_PER_UNIT overrides the choice (tuning experiments; values are clamped to
+    // [1, tiles per atom] by fill_inst)
+    if (const char *env = getenv("SSE_TILES_PER_UNIT"))
+        if (atoi(env) > 0) tpc = atoi(env);
     if (!fill_inst<NK>(prm.inst[0], p, io, tpc, dfull)) return SSE_OK;
     prm.n_inst = 1;
     prm.inject = take_inject(SSE_INJECT_STALL) ? 1 : 0;
