@@ -879,12 +879,20 @@ constexpr int kPostK = 80, kPostKc = kPostK / 8;            // K and its 16-byte
 constexpr uint32_t kPostSbo = kPostKc * 128;                // bytes between 8-row groups
 constexpr uint32_t kPostAPlane = (kRowsMax / 8) * kPostSbo;  // 20480
 constexpr uint32_t kPostBPlane = (32 / 8) * kPostSbo;        // 5120
-constexpr int kTcBarBytes = 192;  // 20 mbarriers, the TMEM address and the flags; the unit index follows
+constexpr int kTcBarBytes = 256;  // 24 mbarriers, the TMEM address and the flags; the unit index follows
+constexpr int kTcEncoders = 96;   // encoding form: the warps of TMEM lane quarter 3 (3, 7, 11)
+constexpr int kPostTiles = 4;     // post-product M tiles per job (three rows r of the block each)
 
 // dH_j[s, t] in shared memory: rows s in blocks of 4 with 4 float2 of padding between
 // blocks, so the epilogue's three row blocks read distinct banks.
 __device__ __forceinline__ int dh_at(int j, int s, int t) { return j * kDhJ + s * 12 + t + (s >> 2) * 4; }
-__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 384;" ::: "memory"); }
+// The epilogue's barrier among the warps that take part in it: all twelve builder warps, or
+// in the encoding form the nine of lane quarters 0-2.
+template <bool ENC>
+__device__ __forceinline__ void builders_sync() {
+    if constexpr (ENC) asm volatile("bar.sync 1, 288;" ::: "memory");
+    else asm volatile("bar.sync 1, 384;" ::: "memory");
+}
 
 // Bytes of one slot's tables in the workspace: the direct Toeplitz table (rows w0 in
 // [1 - TE, Nw + TE - 2]), the pre-product's dH operand and the post-product's conj(dH)
@@ -897,12 +905,11 @@ __host__ __device__ constexpr uint32_t tc_entry_bytes(int nw) { return tc_table_
 // folded Dt, A_pre = the complex product dH_i . G as a real one (row re: (Re dH, -Im dH); row
 // im: (Im dH, Re dH)), and B_post[(s, c'), (j, t, c)] for V conj(dH_j) = (Vr Hr + Vi Hi) +
 // i (Vi Hr - Vr Hi); every value split into bf16 hi + lo.
-template <typename CT>
+template <int NK, typename CT>
 __global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restrict__ D, const CT *__restrict__ dH,
                                                               const int32_t *__restrict__ neigh,
                                                               const int32_t *__restrict__ rev, uint8_t *__restrict__ out,
                                                               int na, int nb, int nqz, int nw, int32_t *status) {
-    constexpr int NK = 5;
     using GG = Geo<NK>;
     extern __shared__ __align__(16) uint8_t tsm[];
     float2 *sDh = (float2 *)tsm;                      // [3][kDhJ] padded dH_j[s, t]
@@ -1011,10 +1018,17 @@ __global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restri
     }
 }
 
-template <typename CT>
+template <int NK, typename CT, bool ENC>
 __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_constant__ MixParams prm) {
-    constexpr int NK = 5;
     using GG = Geo<NK>;
+    constexpr int TE = GG::DA_TE;        // energies per tile of this form (rows (k, j, e): 3 NK TE)
+    constexpr int kVRows = 3 * NK * TE;  // accumulator rows used
+    constexpr int kPostRows = 3 * TE * NK;  // rows (r', e, k) of a post-product tile: three r'
+    static_assert(kVRows <= kRowsMax && kPostRows <= kRowsMax, "tile rows");
+    // The encoding form (ENC) copies raw G blocks and has the warps of TMEM lane quarter 3
+    // encode them for the pre-product; it needs every accumulator and post-product row in
+    // lane quarters 0-2, so that those warps never take part in the epilogue.
+    static_assert(!ENC || (kVRows <= 96 && kPostRows <= 96), "encoding form: rows in lane quarters 0-2");
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ctl = warp == kTcCtlWarp || warp == kTcCtl2Warp || warp == kTcPreWarp;  // MMA-issuing warps
@@ -1030,6 +1044,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint8_t *sApost = smem + prm.off_b;          // epilogue: post-product A tile over the B stages
     uint8_t *sBpost = smem + prm.off_bp;         // post-product B of the slot: conj(dH_j) [hi, lo]
     uint8_t *sRing = smem + prm.off_g;           // [kTcRing] pairs of re-encoded G slices
+    uint8_t *sRaw = smem + prm.off_x;            // encoding form: [kTcRing] pairs of raw G blocks
     uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
     uint8_t *sTab = smem + prm.off_df;           // direct Toeplitz table of the slot
     uint64_t *bars = (uint64_t *)(smem + prm.off_bar);
@@ -1045,14 +1060,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bar_apost = bar_fin + 1;               // post-product A tile built
     uint64_t *bar_slotfree = bar_apost + 1;          // every MMA of the previous slot done
     uint64_t *bar_tab = bar_slotfree + 1;            // the slot's direct table copied in
-    uint32_t *s_tmem = (uint32_t *)(bar_tab + 1);
-    static_assert((2 * kTcRing + 2 * kTcBStages + 9) * 8 + 6 * 4 <= kTcBarBytes, "barrier area");
+    uint64_t *bar_enc = bar_tab + 1;                 // [kTcRing] encoding form: a pair encoded into the ring
+    uint64_t *bar_rawfree = bar_enc + kTcRing;       // [kTcRing] encoding form: a raw pair consumed
+    uint32_t *s_tmem = (uint32_t *)(bar_rawfree + kTcRing);
+    static_assert((4 * kTcRing + 2 * kTcBStages + 9) * 8 + 7 * 4 <= kTcBarBytes, "barrier area");
     // abort flags, each written only by its role (builders: s_abort[0]) before the unit's
     // closing barrier and read by every thread after it
     int *s_abort = (int *)(s_tmem + 1);          // [2]
     int *s_abort_ctl = s_abort + 2;
     int *s_nvalid = s_abort + 3;
     int *s_abort_prd = s_abort + 4;
+    int *s_abort_enc = s_abort + 5;
     long long *s_unit = (long long *)(smem + prm.off_bar + kTcBarBytes);
     int *s_slot = (int *)(s_unit + 1);
     int *s_f = s_slot + kMaxSlots;
@@ -1069,15 +1087,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(bar_tab, 1);
         mbar_init(bar_slotfree, 3);  // the three issuing warps
         mbar_init(bar_fin, 3);       // the three issuing warps
-        mbar_init(bar_apost, kTcBuilders);
+        mbar_init(bar_apost, ENC ? kTcBuilders - kTcEncoders : kTcBuilders);
         mbar_init(&bar_post[0], 1);
         mbar_init(&bar_post[1], 1);
-        for (int b = 0; b < kTcRing; ++b) mbar_init(&bar_empty[b], 1);
+        for (int b = 0; b < kTcRing; ++b) {
+            mbar_init(&bar_empty[b], 1);
+            mbar_init(&bar_enc[b], kTcEncoders);
+            mbar_init(&bar_rawfree[b], kTcEncoders);
+        }
         fence_mbar_init();
         s_abort[0] = 0;
         s_abort[1] = 0;
         *s_abort_ctl = 0;
         *s_abort_prd = 0;
+        *s_abort_enc = 0;
     }
     if (warp == 0) {
         tmem_alloc(s_tmem, kTmemCols);
@@ -1136,9 +1159,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         const int total = (t_end - t_begin) * nvalid * prm.nst;
         if (nvalid == 0) {
             for (int t = t_begin; t < t_end; ++t)
-                for (int x = tid; x < NK * GG::TE * kCh; x += kTcThreads) {
+                for (int x = tid; x < NK * TE * kCh; x += kTcThreads) {
                     const int e = x / (NK * kCh), k = (x / kCh) % NK, c = x % kCh;
-                    const int E = t * GG::TE + e;
+                    const int E = t * TE + e;
                     const size_t idx = (((size_t)k * d.ne + E) * d.na + a) * kCh + c;
                     if (E < d.ne && SSE_BC(idx, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) {
                         CT z;
@@ -1172,7 +1195,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 // of the pair, t / 4, k', t % 4) = 128, K = (re/im of G, u)
                 auto premma = [&]() -> bool {
                     const int slot = pair_ctr % kTcRing;
-                    if (!mbar_wait_bounded(&bar_g[slot], (pair_ctr / kTcRing) & 1, kWaitNs)) return false;
+                    // the pair of slices: copied in (stored form) or encoded by the encoder warps
+                    if (!mbar_wait_bounded(ENC ? &bar_enc[slot] : &bar_g[slot], (pair_ctr / kTcRing) & 1, kWaitNs))
+                        return false;
                     tc_fence_after();
                     constexpr uint32_t idesc_x = idesc_bf16_f32(kRowsMax, 128);
                     const uint64_t boff = (uint64_t)((slot * kTcPairBytes) >> 4);
@@ -1266,7 +1291,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         mma_commit(bar_job);
                         // post-product of the job, one M tile at a time as the builders fill it
                         constexpr uint32_t idesc_p = idesc_bf16_f32(kRowsMax, 32);
-                        for (int q = 0; q < 4 && ok; ++q, ++tile_ctr) {
+                        for (int q = 0; q < kPostTiles && ok; ++q, ++tile_ctr) {
                             if (!(ok = mbar_wait_bounded(bar_apost, tile_ctr & 1, kWaitNs))) break;
                             tc_fence_after();
                             const uint32_t dp = tmem + ((tile_ctr & 1) ? kTcPost1 : kTcPost0);
@@ -1297,9 +1322,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 const int slot_len = (t_end - t_begin) * prm.nst;
                 const long long zero = (long long)d.ne * d.na;  // the zero slice
                 bool ok = true;
-                // one pair of slices (stage offsets o, o + 1 of the slot) into the next ring slot
+                // one pair of slices (stage offsets o, o + 1 of the slot) into the next ring slot;
+                // the encoding form copies the pair's raw G blocks instead, [h][k'][144] values
                 auto issue_pair = [&](int o, int f) -> bool {
                     const int slot = pair_ctr % kTcRing, use = pair_ctr / kTcRing;
+                    if constexpr (ENC) {
+                        // raw slot free: the encoders are done with its previous pair (first use: free)
+                        if (!mbar_wait_bounded(&bar_rawfree[slot], (use & 1) ^ 1, kWaitNs)) return false;
+                        const CT *G = (const CT *)I.G[sign];
+                        uint32_t bytes = 0;
+                        int Eps[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            Eps[h] = -1;
+                            if (o + h < slot_len) {
+                                const int t = t_begin + (o + h) / prm.nst, st = (o + h) % prm.nst;
+                                const int Ep = t * TE - omega_max + st;
+                                if (Ep >= 0 && Ep < d.ne) Eps[h] = Ep;
+                            }
+                            if (Eps[h] >= 0) bytes += NK * kCh * (uint32_t)sizeof(CT);
+                        }
+                        mbar_arrive_expect_tx(&bar_g[slot], bytes);  // no bytes: completes at once
+                        uint8_t *dst = sRaw + (size_t)slot * 2 * NK * kCh * sizeof(CT);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (Eps[h] < 0) continue;
+                            for (int kp = 0; kp < NK; ++kp) {
+                                const size_t src = (((size_t)kp * d.ne + Eps[h]) * d.na + f) * kCh;
+                                if (SSE_BC(src + kCh - 1, (long long)d.nkz * d.ne * d.na * kCh, prm.status))
+                                    bulk_g2s(dst + (h * NK + kp) * kCh * sizeof(CT), G + src, kCh * (uint32_t)sizeof(CT),
+                                             &bar_g[slot]);
+                            }
+                        }
+                        last_g[slot] = pair_ctr++;
+                        return true;
+                    }
                     // ring slot free: the pre-product of its previous pair is done (first use: free)
                     if (!mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs)) return false;
                     mbar_arrive_expect_tx(&bar_g[slot], kTcPairBytes);
@@ -1311,7 +1368,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         long long slice = zero;
                         if (o + h < slot_len) {
                             const int t = t_begin + (o + h) / prm.nst, st = (o + h) % prm.nst;
-                            const int Ep = t * GG::TE - omega_max + st;
+                            const int Ep = t * TE - omega_max + st;
                             if (Ep >= 0 && Ep < d.ne) slice = (long long)Ep * d.na + f;
                         }
                         const uint8_t *sl = gws + slice * kXpSlice;
@@ -1355,12 +1412,70 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 }
             }
             __syncwarp();
+        } else if (ENC && (warp & 3) == 3 && warp < kTcBuilders / 32) {
+            // ================= encoder warps (encoding form): raw G -> pre-product operand =================
+            // Per pair of stages, in the order the bulk-copy warp copies them: wait for the raw
+            // blocks and for the ring slot's previous pre-product, then write the slices -- rows
+            // n' = (t / 4) 4 Nkz + k' 4 + t % 4 (12 Nkz used of 64), K = (re/im of G, u) (24 of
+            // 32), bf16 hi then lo plane, core-matrix order -- and hand the slot to the pre-product.
+            const int et = (warp >> 2) * 32 + lane;  // 0 .. 95
+            const int slot_len = (t_end - t_begin) * prm.nst;
+            const int npairs = (slot_len + 1) / 2;
+            bool ok = true;
+            for (int vs = 0; vs < nvalid && ok; ++vs)
+                for (int pr = 0; pr < npairs && ok; ++pr, ++pair_ctr) {
+                    const int slot = pair_ctr % kTcRing, use = pair_ctr / kTcRing;
+                    if (!(ok = mbar_wait_bounded_sleep(&bar_g[slot], use & 1, kWaitNs))) break;
+                    if (!(ok = mbar_wait_bounded_sleep(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
+                    const uint8_t *raw = sRaw + (size_t)slot * 2 * NK * kCh * sizeof(CT);
+                    uint8_t *dst = sRing + slot * kTcPairBytes;
+                    for (int it = et; it < 2 * 64 * 4; it += kTcEncoders) {  // (stage h, row n', K group)
+                        const int h = it >> 8, np = (it >> 2) & 63, kg = it & 3;
+                        const int o2 = 2 * pr + h;
+                        bool live = np < 12 * NK && o2 < slot_len;
+                        if (live) {
+                            const int t = t_begin + o2 / prm.nst, st = o2 % prm.nst;
+                            const int Ep = t * TE - omega_max + st;
+                            live = Ep >= 0 && Ep < d.ne;
+                        }
+                        float v[8];
+#pragma unroll
+                        for (int xx = 0; xx < 8; ++xx) {
+                            const int kk = kg * 8 + xx;
+                            float val = 0.f;
+                            if (live && kk < 24) {
+                                const int blk = np / (4 * NK), kp = (np % (4 * NK)) / 4, t = 4 * blk + np % 4;
+                                const int pc = kk / 12, u = kk % 12;
+                                const float2 c = load_c32_smem((const CT *)raw + (h * NK + kp) * kCh + u * 12 + t);
+                                val = pc ? c.y : c.x;
+                            }
+                            v[xx] = val;
+                        }
+                        uint32_t hv[4], lv[4];
+#pragma unroll
+                        for (int xx = 0; xx < 4; ++xx) {
+                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
+                            hv[xx] = hl.x;
+                            lv[xx] = hl.y;
+                        }
+                        uint8_t *pd = dst + h * 4096 + (np >> 3) * 512 + kg * 128 + (np & 7) * 16;
+                        *(uint4 *)pd = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *(uint4 *)(pd + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    }
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bar_rawfree[slot]);
+                    mbar_arrive(&bar_enc[slot]);
+                }
+            if (!ok) {
+                if (lane == 0) *s_abort_enc = 1;
+                atomicOr(prm.status, kStatusTimeout);
+            }
         } else if (warp < kTcBuilders / 32) {
             // ================= builder warps =================
             Pos cur{t_begin, 0, 0};
             const int slot_len = (t_end - t_begin) * prm.nst;
-            int o = 0;           // stage index within the slot
-            uint32_t xnext[15];  // X warps: K row of the pair's second stage, kept until then
+            int o = 0;                // stage index within the slot
+            uint32_t xnext[3 * NK];   // X warps: K row of the pair's second stage, kept until then
             const int q4 = warp & 3, cb = warp >> 2;
             const bool xw = q4 < 3;  // warps whose lane quarter holds X rows
             // A failed wait marks this builder bad and skips its later waits; builders never
@@ -1375,13 +1490,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             for (int g = 0; g < total; ++g, advance(cur), o = (o + 1 == slot_len) ? 0 : o + 1) {
                 const int t = cur.t, vs = cur.vs, st = cur.st;
                 const int gg = g_base + g, sb = gg % kTcBStages, use = gg / kTcBStages;
-                const int E0 = t * GG::TE;
+                const int E0 = t * TE;
                 const bool job_first = st == 0, job_last = st == prm.nst - 1;
-                if (job_first && vs > 0) {
+                if (job_first && vs > 0 && (!ENC || xw)) {
                     // the job's epilogue adds to Sigma: bring those lines to L2 while the job runs
                     constexpr int kLines = (kCh * (int)sizeof(CT) + 127) / 128;
-                    for (int x = tid; x < NK * GG::TE * kLines; x += kTcBuilders) {
-                        const int pt = x / kLines, ln = x % kLines, k = pt / GG::TE, E = E0 + pt % GG::TE;
+                    constexpr int kPrefetchers = ENC ? kTcBuilders - kTcEncoders : kTcBuilders;
+                    const int ptid = ENC ? (warp >> 2) * 96 + q4 * 32 + lane : tid;
+                    for (int x = ptid; x < NK * TE * kLines; x += kPrefetchers) {
+                        const int pt = x / kLines, ln = x % kLines, k = pt / TE, E = E0 + pt % TE;
                         if (E < d.ne && SSE_BC((((size_t)k * d.ne + E) * d.na + a) * kCh, (long long)d.nkz * d.ne * d.na * kCh, prm.status))
                             prefetch_l2((const uint8_t *)(S + (((size_t)k * d.ne + E) * d.na + a) * kCh) + ln * 128);
                     }
@@ -1398,50 +1515,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     tc_fence_after();
                 }
                 if (pair_first) ++pair_ctr;
-                uint32_t xa[10], xb[10];  // rows (i0 | i1) and (i2 | zero), repetition k = k'
+                uint32_t xa[2 * NK], xb[2 * NK];  // rows (i0 | i1) and (i2 | zero), repetition k = k'
                 if (xw) {
                     if (pair_first) {
-                        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + kTcPre + 20 * cb;
-                        using R8 = uint32_t(&)[8];
-                        using R2 = uint32_t(&)[2];
-                        tmem_ld16x128_x4(ta, reinterpret_cast<R8>(xa[0]));
-                        tmem_ld16x128_x1(ta + 16, reinterpret_cast<R2>(xa[8]));
-                        tmem_ld16x128_x4(ta + (16u << 16), reinterpret_cast<R8>(xb[0]));
-                        tmem_ld16x128_x1(ta + (16u << 16) + 16, reinterpret_cast<R2>(xb[8]));
-                        uint32_t na[10], nb[10];
-                        tmem_ld16x128_x4(ta + 64, reinterpret_cast<R8>(na[0]));
-                        tmem_ld16x128_x1(ta + 64 + 16, reinterpret_cast<R2>(na[8]));
-                        tmem_ld16x128_x4(ta + 64 + (16u << 16), reinterpret_cast<R8>(nb[0]));
-                        tmem_ld16x128_x1(ta + 64 + (16u << 16) + 16, reinterpret_cast<R2>(nb[8]));
+                        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + kTcPre + 4 * NK * cb;
+                        tmem_ld16x128_reps<NK>(ta, xa);
+                        tmem_ld16x128_reps<NK>(ta + (16u << 16), xb);
+                        uint32_t na[2 * NK], nb[2 * NK];
+                        tmem_ld16x128_reps<NK>(ta + 64, na);
+                        tmem_ld16x128_reps<NK>(ta + 64 + (16u << 16), nb);
                         tmem_ld_wait();
                         tc_fence_before();
 #pragma unroll
-                        for (int k = 0; k < 5; ++k) {
+                        for (int k = 0; k < NK; ++k) {
                             xnext[k] = na[2 * k];
-                            xnext[5 + k] = na[2 * k + 1];
-                            xnext[10 + k] = nb[2 * k];
+                            xnext[NK + k] = na[2 * k + 1];
+                            xnext[2 * NK + k] = nb[2 * k];
                         }
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 5; ++k) {
+                        for (int k = 0; k < NK; ++k) {
                             xa[2 * k] = xnext[k];
-                            xa[2 * k + 1] = xnext[5 + k];
-                            xb[2 * k] = xnext[10 + k];
+                            xa[2 * k + 1] = xnext[NK + k];
+                            xb[2 * k] = xnext[2 * NK + k];
                         }
                     }
                 }
                 // ---- the B buffer must be free: the main MMAs of its previous stage complete ----
                 if (xw && use > 0) bwait(&bar_mma[sb], (use - 1) & 1);
                 if (xw) {
-                    // K row kk = i * Nkz + k' (15 used, 16th zero), split into bf16 hi / lo
+                    // K row kk = i * Nkz + k' (3 Nkz used, the rest of the 16 zero), split into bf16 hi / lo
                     float v[16];
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
+                    for (int k = 0; k < NK; ++k) {
                         v[k] = __uint_as_float(xa[2 * k]);
-                        v[5 + k] = __uint_as_float(xa[2 * k + 1]);
-                        v[10 + k] = __uint_as_float(xb[2 * k]);
+                        v[NK + k] = __uint_as_float(xa[2 * k + 1]);
+                        v[2 * NK + k] = __uint_as_float(xb[2 * k]);
                     }
-                    v[15] = 0.f;
+#pragma unroll
+                    for (int k = 3 * NK; k < 16; ++k) v[k] = 0.f;
                     uint32_t hv[8], lv[8];
 #pragma unroll
                     for (int x = 0; x < 8; ++x) {
@@ -1468,26 +1580,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     // barrier until then
                     if (xw) bwait(bar_job, job_ctr & 1);
                     ++job_ctr;
-                    builders_sync();  // every builder is done with B before the A tile overlays it
+                    builders_sync<ENC>();  // every builder is done with B before the A tile overlays it
                     tc_fence_after();
                     const bool first_slot = vs == 0;
                     // A-tile role: warp -> (lane quarter, row r' of the tile); lane -> accumulator row
                     const int aq = warp & 3, arl = warp >> 2;
                     const int am = aq * 32 + lane;
-                    const int ak = am / 24, aj = (am / 8) % 3, ae = am % 8;
+                    const int ak = am / (3 * TE), aj = (am / TE) % 3, ae = am % TE;
                     // drain role: warp -> (lane quarter = tile rows, 8 of the 24 columns = 4 values s)
                     const int dq = warp & 3, dsub = warp >> 2;
                     const int drow = dq * 32 + lane;  // tile row (r', e, k)
-                    const int drl = drow / 40, de = (drow / 5) % 8, dk = drow % 5;
-                    const bool dlive = drow < 120 && E0 + de < d.ne;
+                    const int drl = drow / (TE * NK), de = (drow / NK) % TE, dk = drow % NK;
+                    const bool dlive = drow < kPostRows && E0 + de < d.ne;
                     CT *dst = S;
                     // Tile q: its A is built once the MMAs of tile q - 1 are done (one A buffer);
                     // the accumulator columns it needs are loaded before that wait, and tile
                     // q - 1's result is drained and added to Sigma after tile q is handed to the MMAs.
-                    for (int q = 0; q <= 4; ++q) {
+                    for (int q = 0; q <= kPostTiles; ++q) {
                         const int tq = tile_ctr + q;  // CTA-wide index of tile q
                         uint32_t vr[12], vi[12];
-                        if (q < 4) {
+                        if (q < kPostTiles) {
                             const uint32_t ta = tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)((3 * q + arl) * 12);
                             tmem_ld8(ta, *reinterpret_cast<float(*)[8]>(vr));
                             tmem_ld4(ta + 8, *reinterpret_cast<uint32_t(*)[4]>(vr + 8));
@@ -1500,9 +1612,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tc_fence_after();
                         }
                         tmem_ld_wait();
-                        if (q < 4 && am < 120) {
+                        if (q < kPostTiles && am < kVRows) {
                             // ---- A tile q: rows (r', e, k), K = (j, t, re/im), bf16 hi / lo ----
-                            const int row = arl * 40 + ae * 5 + ak;
+                            const int row = arl * (TE * NK) + ae * NK + ak;
                             uint8_t *rbase = sApost + (row >> 3) * kPostSbo + (row & 7) * 16;
 #pragma unroll
                             for (int cc = 0; cc < 3; ++cc) {
@@ -1524,7 +1636,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             }
                         }
                         tc_fence_before();
-                        if (q < 4) {
+                        if (q < kPostTiles) {
                             fence_proxy_async_smem();
                             mbar_arrive(bar_apost);
                         }
@@ -1548,18 +1660,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                                 else slot_add(dst + s2, v);
                             }
                         }
-                        if (q < 4)
+                        if (q < kPostTiles)
                             dst = S + (((size_t)dk * d.ne + (dlive ? E0 + de : 0)) * d.na + a) * kCh + (3 * q + drl) * 12 +
                                   4 * dsub;
                     }
-                    tile_ctr += 4;
+                    tile_ctr += kPostTiles;
                 }
             }
             if (bad) s_abort[0] = 1;  // read by every thread after the unit's closing barrier
         }
         g_base += total;
         __syncthreads();
-        if (s_abort[0] || s_abort[1] || *s_abort_ctl || *s_abort_prd) {
+        if (s_abort[0] || s_abort[1] || *s_abort_ctl || *s_abort_prd || *s_abort_enc) {
             abort = true;
             break;
         }
@@ -1584,10 +1696,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 }
 
 // Shared memory of the warp-specialised kernel: the B stages (the epilogue's post-product
-// A tile overlays them), the G-slice ring, the pre-product's dH operand, the direct table,
-// the post-product's conj(dH) operand and the barriers.
-uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
-    using GG = Geo<5>;
+// A tile overlays them), the G-slice ring, in the encoding form the raw G ring, the
+// pre-product's dH operand, the direct table, the post-product's conj(dH) operand and the
+// barriers.
+template <int NK, bool ENC>
+uint32_t tc_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
+    using GG = Geo<NK>;
     uint32_t off = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
         off = (off + align - 1) / align * align;
@@ -1598,8 +1712,8 @@ uint32_t tc_smem_bytes(const Dims &d, MixParams &prm) {
     const uint32_t bsz = kTcBStages * 4 * GG::DA_B_PLANE;
     const uint32_t nv = 2 * kPostAPlane;
     prm.off_b = take(bsz > nv ? bsz : nv, 1024);
-    prm.off_x = 0;
     prm.off_g = take(kTcRing * kTcPairBytes, 1024);
+    prm.off_x = ENC ? take((uint32_t)(kTcRing * 2 * NK * kCh * cbytes), 128) : 0;
     prm.off_a = take(2 * 8192, 1024);
     const uint32_t rows = (uint32_t)(d.nw + 2 * GG::DA_TE - 2);
     prm.off_df = take(2u * 2u * GG::DA_GROUPS * 2u * rows * 16u, 1024);
@@ -1656,9 +1770,10 @@ uint32_t mixed_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
 
 // One instance descriptor from a plan and its buffers; the requested signs are packed
 // into slots 0 and 1.  Returns false when no sign is requested.
-template <int NK>
+template <int NK, bool V3>
 bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc, bool dfull) {
     using GG = Geo<NK>;
+    constexpr int TE = V3 ? GG::DA_TE : GG::TE;
     const bool do_gt = io.S_gt != nullptr, do_lt = io.S_lt != nullptr;
     I.nsign = (int)do_gt + (int)do_lt;
     if (I.nsign == 0) return false;
@@ -1675,13 +1790,14 @@ bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc, bool dfull
     I.ne = p.d.ne;
     I.nb = p.d.nb;
     I.nqz = p.d.nqz;
-    I.ntiles = (I.ne + GG::TE - 1) / GG::TE;
+    I.ntiles = (I.ne + TE - 1) / TE;
     I.tiles_per_cta = tpc < 1 ? 1 : (tpc > I.ntiles ? I.ntiles : tpc);
-    const size_t sign_bytes = ((size_t)p.d.ne * p.d.na + 1) * 8192;
+    // the workspace: stored G slices (Nkz = 5 only), then the slot tables
+    const size_t sign_bytes = NK == 5 ? ((size_t)p.d.ne * p.d.na + 1) * 8192 : 0;
     const size_t tab_sign = (size_t)p.d.na * p.d.nb * tc_entry_bytes(p.d.nw);
     const uint8_t *ws = (const uint8_t *)p.mixed_ws;
-    I.gws[0] = ws ? ws + (do_gt ? 0 : sign_bytes) : nullptr;
-    I.gws[1] = ws ? ws + sign_bytes : nullptr;
+    I.gws[0] = (ws && NK == 5) ? ws + (do_gt ? 0 : sign_bytes) : nullptr;
+    I.gws[1] = (ws && NK == 5) ? ws + sign_bytes : nullptr;
     I.sws[0] = ws ? ws + 2 * sign_bytes + (do_gt ? 0 : tab_sign) : nullptr;
     I.sws[1] = ws ? ws + 2 * sign_bytes + tab_sign : nullptr;
     I.nchunks = (I.ntiles + I.tiles_per_cta - 1) / I.tiles_per_cta;
@@ -1693,7 +1809,8 @@ long long inst_units(const InstDesc &I) { return (long long)I.nsign * I.na * I.n
 template <int NK, typename CT, bool V3>
 sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *status) {
     using GG = Geo<NK>;
-    smem = V3 ? tc_smem_bytes(d, prm) : mixed_smem_bytes<NK>(d, sizeof(CT), prm);
+    constexpr bool ENC = V3 && NK < 5;  // below Nkz = 5 the warp-specialised form encodes G itself
+    smem = V3 ? tc_smem_bytes<NK, ENC>(d, sizeof(CT), prm) : mixed_smem_bytes<NK>(d, sizeof(CT), prm);
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
         return SSE_E_INVALID_ARG;
@@ -1702,10 +1819,10 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
     prm.nkz = d.nkz;
     prm.nw = d.nw;
     prm.omega_first = d.omega_first;
-    prm.nst = (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
+    prm.nst = V3 ? GG::DA_TE + d.nw - 1 : (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
     cudaError_t e;
     if constexpr (V3)
-        e = cudaFuncSetAttribute(sse_tc_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(sse_tc_kernel<NK, CT, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else
         e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
@@ -1715,23 +1832,24 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
 
 // Fill the plan's workspace for every requested sign of one instance: G re-encoded for the
 // pre-product and the slot tables.
-template <typename CT>
+template <int NK, typename CT>
 sse_status split_g(const Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
-    const size_t sign_bytes = ((size_t)p.d.ne * p.d.na + 1) * 8192;
+    const size_t sign_bytes = NK == 5 ? ((size_t)p.d.ne * p.d.na + 1) * 8192 : 0;
     const size_t tab_sign = (size_t)p.d.na * p.d.nb * tc_entry_bytes(p.d.nw);
     const void *gs[2] = {io.S_gt ? io.G_gt : nullptr, io.S_lt ? io.G_lt : nullptr};
     const void *ds[2] = {io.D_gt, io.D_lt};
     const uint32_t tsmem = 3 * kDhJ * 8 + 5 * p.d.nw * 9 * 8;
-    if (p.d.nkz != 5) return set_error("mixed mode: the tensor-core form needs Nkz = 5"), SSE_E_INVALID_ARG;
+    if (p.d.nkz != NK) return set_error("mixed mode: workspace pass for the wrong Nkz"), SSE_E_INVALID_ARG;
     for (int s = 0; s < 2; ++s) {
         if (!gs[s]) continue;
         const long long slices = (long long)p.d.ne * p.d.na;
         if (slices > 0x7fffffffLL || (long long)p.d.na * p.d.nb > 0x7fffffffLL)
             return set_error("mixed mode: instance too large"), SSE_E_INVALID_ARG;
         uint8_t *ws = (uint8_t *)p.mixed_ws;
-        sse_split_g_kernel<CT><<<(unsigned)slices, 256, 0, st>>>((const CT *)gs[s], ws + s * sign_bytes, p.d.ne,
-                                                                p.d.na, p.d.nkz);
-        sse_slot_tables_kernel<CT><<<(unsigned)(p.d.na * p.d.nb), 256, tsmem, st>>>(
+        if (NK == 5)  // below Nkz = 5 the kernel encodes G itself
+            sse_split_g_kernel<CT><<<(unsigned)slices, 256, 0, st>>>((const CT *)gs[s], ws + s * sign_bytes, p.d.ne,
+                                                                    p.d.na, p.d.nkz);
+        sse_slot_tables_kernel<NK, CT><<<(unsigned)(p.d.na * p.d.nb), 256, tsmem, st>>>(
             (const CT *)ds[s], (const CT *)p.geo.dH, p.geo.neigh, dfull ? p.d_rev : nullptr,
             ws + 2 * sign_bytes + s * tab_sign, p.d.na, p.d.nb, p.d.nqz, p.d.nw, p.d_status);
     }
@@ -1752,18 +1870,26 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
     sse_status rs = prepare<NK, CT, V3>(prm, smem, p.d, p.d_status);
     if (rs != SSE_OK) return rs;
     if (!aligned16(io)) return set_error("mixed mode: G buffers must be 16-byte aligned"), SSE_E_INVALID_ARG;
-    // tiles per unit: enough units for several waves over the SMs
-    int sms = 148;
+    // tiles per unit: enough units for several waves over the SMs; the warp-specialised form
+    // also keeps the Sigma tiles of the units in flight (one per SM) within half the L2, so
+    // that a unit's sum over neighbour slots reduces into lines still in L2
+    int sms = 148, l2 = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-    const int ntiles = (p.d.ne + GG::TE - 1) / GG::TE;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p.device);
+    constexpr int TE = V3 ? GG::DA_TE : GG::TE;
+    const int ntiles = (p.d.ne + TE - 1) / TE;
     const long long per_chunk = (long long)((io.S_gt != nullptr) + (io.S_lt != nullptr)) * p.d.na;
     int tpc = ntiles;
     while (tpc > 1 && per_chunk * ((ntiles + tpc - 1) / tpc) < 8LL * sms) tpc = (tpc + 1) / 2;
+    if (V3 && l2 > 0) {
+        const long long tile_bytes = (long long)TE * NK * kCh * sizeof(CT);
+        while (tpc > 1 && (long long)sms * tpc * tile_bytes > l2 / 2) tpc = (tpc + 1) / 2;
+    }
     // SSE_TILES_PER_UNIT overrides the choice (tuning experiments; values are clamped to
     // [1, tiles per atom] by fill_inst)
     if (const char *env = getenv("SSE_TILES_PER_UNIT"))
         if (atoi(env) > 0) tpc = atoi(env);
-    if (!fill_inst<NK>(prm.inst[0], p, io, tpc, dfull)) return SSE_OK;
+    if (!fill_inst<NK, V3>(prm.inst[0], p, io, tpc, dfull)) return SSE_OK;
     prm.n_inst = 1;
     prm.inject = take_inject(SSE_INJECT_STALL) ? 1 : 0;
     prm.inst[0].unit_begin = 0;
@@ -1773,18 +1899,18 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
     const int ts = timing_slot(p);
     timing_mark(p, ts, 0, st);
     if (V3) {
-        rs = split_g<CT>(p, io, st, dfull);
+        rs = split_g<NK, CT>(p, io, st, dfull);
         if (rs != SSE_OK) return rs;
     }
     timing_mark(p, ts, 1, st);
     if constexpr (V3)
-        sse_tc_kernel<CT><<<(unsigned)prm.total_units, kTcThreads, smem, st>>>(prm);
+        sse_tc_kernel<NK, CT, (NK < 5)><<<(unsigned)prm.total_units, kTcThreads, smem, st>>>(prm);
     else
         sse_mixed_kernel<NK, CT><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
     timing_mark(p, ts, 2, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch sse_mixed_kernel");
-    p.tile_e = GG::TE;
+    p.tile_e = TE;
     return SSE_OK;
 }
 
@@ -1805,9 +1931,9 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
             const Plan &p = *plans[order[x]];
             const sse_io &io = ios[order[x]];
             if (!aligned16(io)) return set_error("mixed mode: G buffers must be 16-byte aligned"), SSE_E_INVALID_ARG;
-            if (!fill_inst<NK>(prm.inst[m], p, io, tpc, false)) continue;
+            if (!fill_inst<NK, V3>(prm.inst[m], p, io, tpc, false)) continue;
             if (V3) {
-                rs = split_g<CT>(p, io, st, false);
+                rs = split_g<NK, CT>(p, io, st, false);
                 if (rs != SSE_OK) return rs;
             }
             prm.inst[m].unit_begin = units;
@@ -1823,7 +1949,7 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
         if (e != cudaSuccess) return cuda_fail(e, "reset the work counter");
         const long long grid = units < sms ? units : sms;
         if constexpr (V3)
-            sse_tc_kernel<CT><<<(unsigned)grid, kTcThreads, smem, st>>>(prm);
+            sse_tc_kernel<NK, CT, (NK < 5)><<<(unsigned)grid, kTcThreads, smem, st>>>(prm);
         else
             sse_mixed_kernel<NK, CT><<<(unsigned)grid, kThreads, smem, st>>>(prm);
         e = cudaGetLastError();
@@ -1834,46 +1960,56 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
 
 template <typename CT>
 sse_status launch_dtype(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
+    // the warp-specialised form when the plan has its workspace, else the single-role form
+    const bool ws = p.mixed_ws != nullptr;
     switch (p.d.nkz) {
-        case 1: return launch_nk<1, CT, false>(p, io, st, dfull);
-        case 2: return launch_nk<2, CT, false>(p, io, st, dfull);
-        case 3: return launch_nk<3, CT, false>(p, io, st, dfull);
-        case 4: return launch_nk<4, CT, false>(p, io, st, dfull);
-        case 5:
-            return p.mixed_ws ? launch_nk<5, CT, true>(p, io, st, dfull) : launch_nk<5, CT, false>(p, io, st, dfull);
+        case 1: return ws ? launch_nk<1, CT, true>(p, io, st, dfull) : launch_nk<1, CT, false>(p, io, st, dfull);
+        case 2: return ws ? launch_nk<2, CT, true>(p, io, st, dfull) : launch_nk<2, CT, false>(p, io, st, dfull);
+        case 3: return ws ? launch_nk<3, CT, true>(p, io, st, dfull) : launch_nk<3, CT, false>(p, io, st, dfull);
+        case 4: return ws ? launch_nk<4, CT, true>(p, io, st, dfull) : launch_nk<4, CT, false>(p, io, st, dfull);
+        case 5: return ws ? launch_nk<5, CT, true>(p, io, st, dfull) : launch_nk<5, CT, false>(p, io, st, dfull);
         default:
             set_error("mixed mode supports Nkz <= 5 (got %d)", p.d.nkz);
             return SSE_E_INVALID_ARG;
     }
 }
 
+template <int NK, typename CT>
+sse_status launch_batch_form(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
+                             int32_t *queue, int32_t *status, cudaStream_t st) {
+    // the warp-specialised form needs each plan's workspace for itself: every plan once
+    bool all_ws = true;
+    for (int x = 0; x < n && all_ws; ++x) {
+        all_ws = plans[order[x]]->mixed_ws != nullptr;
+        for (int y = 0; y < x && all_ws; ++y) all_ws = plans[order[y]] != plans[order[x]];
+    }
+    return all_ws ? launch_batch_nk<NK, CT, true>(plans, ios, order, n, tpc, queue, status, st)
+                  : launch_batch_nk<NK, CT, false>(plans, ios, order, n, tpc, queue, status, st);
+}
+
 template <typename CT>
 sse_status launch_batch_dtype(Plan *const *plans, const sse_io *ios, const int *order, int n, int tpc,
                               int32_t *queue, int32_t *status, cudaStream_t st) {
     switch (plans[order[0]]->d.nkz) {
-        case 1: return launch_batch_nk<1, CT, false>(plans, ios, order, n, tpc, queue, status, st);
-        case 2: return launch_batch_nk<2, CT, false>(plans, ios, order, n, tpc, queue, status, st);
-        case 3: return launch_batch_nk<3, CT, false>(plans, ios, order, n, tpc, queue, status, st);
-        case 4: return launch_batch_nk<4, CT, false>(plans, ios, order, n, tpc, queue, status, st);
-        case 5: {
-            // the pre-product form needs each plan's workspace for itself: every plan once
-            bool all_ws = true;
-            for (int x = 0; x < n && all_ws; ++x) {
-                all_ws = plans[order[x]]->mixed_ws != nullptr;
-                for (int y = 0; y < x && all_ws; ++y) all_ws = plans[order[y]] != plans[order[x]];
-            }
-            return all_ws ? launch_batch_nk<5, CT, true>(plans, ios, order, n, tpc, queue, status, st)
-                          : launch_batch_nk<5, CT, false>(plans, ios, order, n, tpc, queue, status, st);
-        }
+        case 1: return launch_batch_form<1, CT>(plans, ios, order, n, tpc, queue, status, st);
+        case 2: return launch_batch_form<2, CT>(plans, ios, order, n, tpc, queue, status, st);
+        case 3: return launch_batch_form<3, CT>(plans, ios, order, n, tpc, queue, status, st);
+        case 4: return launch_batch_form<4, CT>(plans, ios, order, n, tpc, queue, status, st);
+        case 5: return launch_batch_form<5, CT>(plans, ios, order, n, tpc, queue, status, st);
         default:
             set_error("mixed mode supports Nkz <= 5");
             return SSE_E_INVALID_ARG;
     }
 }
 
+// Shared memory of both forms for one Nkz: the single-role form's (the plan is valid only if
+// it fits: the no-alloc entry and batches holding a plan twice use it) and the
+// warp-specialised form's.
 template <int NK>
-int tile_e_of() {
-    return Geo<NK>::TE;
+void smem_of(const Dims &d, size_t cb, uint32_t &single, uint32_t &ws) {
+    MixParams prm{};
+    single = mixed_smem_bytes<NK>(d, cb, prm);
+    ws = tc_smem_bytes<NK, (NK < 5)>(d, cb, prm);
 }
 
 }  // namespace
@@ -1888,26 +2024,25 @@ sse_status mixed_plan_init(Plan &p) {
         set_error("mixed mode supports nb_max <= %d (got %d)", kMaxSlots, d.nb);
         return SSE_E_INVALID_ARG;
     }
-    MixParams prm{};
-    uint32_t smem = 0;
+    uint32_t smem = 0, smem_ws = 0;
     const size_t cb = elem_bytes(p.geo.dtype);
     switch (d.nkz) {
-        case 1: smem = mixed_smem_bytes<1>(d, cb, prm); p.tile_e = tile_e_of<1>(); break;
-        case 2: smem = mixed_smem_bytes<2>(d, cb, prm); p.tile_e = tile_e_of<2>(); break;
-        case 3: smem = mixed_smem_bytes<3>(d, cb, prm); p.tile_e = tile_e_of<3>(); break;
-        case 4: smem = mixed_smem_bytes<4>(d, cb, prm); p.tile_e = tile_e_of<4>(); break;
-        default: smem = mixed_smem_bytes<5>(d, cb, prm); p.tile_e = tile_e_of<5>(); break;
+        case 1: smem_of<1>(d, cb, smem, smem_ws); p.tile_e = Geo<1>::TE; break;
+        case 2: smem_of<2>(d, cb, smem, smem_ws); p.tile_e = Geo<2>::TE; break;
+        case 3: smem_of<3>(d, cb, smem, smem_ws); p.tile_e = Geo<3>::TE; break;
+        case 4: smem_of<4>(d, cb, smem, smem_ws); p.tile_e = Geo<4>::TE; break;
+        default: smem_of<5>(d, cb, smem, smem_ws); p.tile_e = Geo<5>::TE; break;
     }
     if (smem > 232448u) {
         set_error("mixed mode: Nkz=%d, Nw=%d needs more shared memory than one SM has", d.nkz, d.nw);
         return SSE_E_INVALID_ARG;
     }
-    // Nkz = 5: the warp-specialised tensor-core form when its tiles fit (Nw <= 40), with a
-    // workspace; otherwise the direct form above
-    if (d.nkz == 5 && tc_smem_bytes(d, prm) <= 232448u) {
-        // workspace of the tensor-core form, per sign: G re-encoded for the pre-product plus a
-        // zero slice, then the slot tables of every (atom, slot)
-        const size_t sign_bytes = ((size_t)d.ne * d.na + 1) * 8192;
+    // the warp-specialised tensor-core form when its tiles fit (Nw <= 50 at Nkz = 5), with a
+    // workspace; otherwise the single-role form above
+    if (smem_ws <= 232448u) {
+        // workspace, per sign: at Nkz = 5 G re-encoded for the pre-product plus a zero slice
+        // (below that the kernel encodes G itself), then the slot tables of every (atom, slot)
+        const size_t sign_bytes = d.nkz == 5 ? ((size_t)d.ne * d.na + 1) * 8192 : 0;
         const size_t tab_sign = (size_t)d.na * d.nb * tc_entry_bytes(d.nw);
         const size_t bytes = 2 * sign_bytes + 2 * tab_sign;
         cudaError_t e = take_inject(SSE_INJECT_ALLOC_FAIL) ? cudaErrorMemoryAllocation : cudaMalloc(&p.mixed_ws, bytes);
@@ -1919,7 +2054,8 @@ sse_status mixed_plan_init(Plan &p) {
         }
         p.mixed_ws_bytes = bytes;
         p.workspace_bytes += (int64_t)p.mixed_ws_bytes;
-        for (int s2 = 0; s2 < 2; ++s2) {
+        p.tile_e = Geo<5>::DA_TE;
+        for (int s2 = 0; s2 < 2 && sign_bytes > 0; ++s2) {
             e = cudaMemset((uint8_t *)p.mixed_ws + s2 * sign_bytes + (size_t)d.ne * d.na * 8192, 0, 8192);
             if (e != cudaSuccess) return cuda_fail(e, "clear the zero slice");
         }

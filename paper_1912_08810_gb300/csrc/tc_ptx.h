@@ -197,6 +197,24 @@ __device__ __forceinline__ void tmem_ld16x128_x1(uint32_t taddr, uint32_t (&r)[2
     asm volatile("tcgen05.ld.sync.aligned.16x128b.x1.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld16x128_x2(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.16x128b.x2.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+// NK repetitions of the 16-lane shape from column `taddr` on: r[2k] and r[2k + 1] as above.
+template <int NK>
+__device__ __forceinline__ void tmem_ld16x128_reps(uint32_t taddr, uint32_t (&r)[2 * NK]) {
+    using R8 = uint32_t(&)[8];
+    using R4 = uint32_t(&)[4];
+    using R2 = uint32_t(&)[2];
+    if constexpr (NK >= 4) tmem_ld16x128_x4(taddr, reinterpret_cast<R8>(r[0]));
+    if constexpr (NK == 5) tmem_ld16x128_x1(taddr + 16, reinterpret_cast<R2>(r[8]));
+    if constexpr (NK == 2 || NK == 3) tmem_ld16x128_x2(taddr, reinterpret_cast<R4>(r[0]));
+    if constexpr (NK == 3) tmem_ld16x128_x1(taddr + 8, reinterpret_cast<R2>(r[4]));
+    if constexpr (NK == 1) tmem_ld16x128_x1(taddr, reinterpret_cast<R2>(r[0]));
+}
+
 // 32 lanes x 8 columns of 32-bit values: thread t of the warp gets lane (base + t).
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
@@ -288,6 +306,13 @@ template <>
 __device__ __forceinline__ float2 load_c32<float2>(const float2 *p) {
     return __ldg(p);
 }
+
+// A complex value in shared memory as FP32 (complex128 values rounded to nearest).
+__device__ __forceinline__ float2 load_c32_smem(const double2 *p) {
+    const double2 v = *p;
+    return make_float2(f64_to_f32(v.x), f64_to_f32(v.y));
+}
+__device__ __forceinline__ float2 load_c32_smem(const float2 *p) { return *p; }
 
 // (hi, lo) split of x into two bf16 values with x ~= hi + lo (both rounded to nearest).
 // Returns the pair packed as one word: hi in the low half, lo in the high half.
