@@ -72,6 +72,8 @@ def parse_args():
                     help="requests of the serving leg (Poisson arrivals; 0: skip the leg)")
     ap.add_argument("--leg-steps", type=int, default=20,
                     help="timed repetitions of each leg (p50/p99 need at least 20)")
+    ap.add_argument("--no-pi", action="store_true",
+                    help="skip the phonon self-energy leg (Pi, FP64; Nkz=Nqz=5, NE=256, Nw=32, Na=152)")
     return ap.parse_args()
 
 
@@ -457,6 +459,9 @@ def run_ours(args):
     if not args.no_batched and form == "mixed":
         out["batched"] = run_batched(args, stream, peaks, uuid)
         out["gpu_launches"] += out["batched"]["gpu_launches"]
+    if not args.no_pi:
+        out["pi"] = run_pi(args, stream, uuid)
+        out["gpu_launches"] += out["pi"]["gpu_launches"]
     if args.serving and form == "mixed":
         out["serving"] = run_serving(args.serving, uuid)
         out["gpu_launches"] += out["serving"]["gpu_launches"]
@@ -504,6 +509,52 @@ def run_precision(args, stream, peaks, uuid):
                         "algorithmic_flops_per_launch": flops}}
     plan.close()
     del inst, S
+    torch.cuda.empty_cache()
+    return res
+
+
+def pi_flops(geo, neigh):
+    """Algorithmic real flops of Pi per sign: per bond, the nine traces per (q, w, k, valid E)
+    as 144-channel dot products of V_i = dH_i^+ G_aa and U_j = dH_j G_bb (formed once per
+    (k, E) each: 6 products of 12^3), 8 flops per complex MAC."""
+    bonds = int((neigh >= 0).sum())
+    valid = sum(max(0, geo.ne - abs(w + geo.omega_first)) for w in range(geo.nw))
+    cmacs = bonds * (geo.nqz * valid * geo.nkz * 9 * 144 + geo.nkz * geo.ne * 6 * 1728)
+    return 8.0 * cmacs
+
+
+def run_pi(args, stream, uuid):
+    """The phonon self-energy Pi^> and Pi^< (Eqs. 4-5) in FP64 on Nkz=Nqz=5, NE=256, Nw=32,
+    Na=152, Nb=4 chain neighbours, complex128 (seed 5, drawn on the device): one CTA per
+    (atom, sign), two per SM.  FP64-pipe bound."""
+    import torch
+
+    from paper_1912_08810_gb300 import inputs, sse
+    geo = inputs.Geometry(nkz=5, nqz=5, ne=256, nw=32, na=152, nb=4)
+    inst = inputs.make_instance_torch(geo, 5, dtype=torch.complex128)
+    plan = sse.Plan(inst["neigh"], inst["dH"], nkz=geo.nkz, nqz=geo.nqz, ne=geo.ne, nw=geo.nw, mode="fp64")
+    shape = (geo.nqz, geo.nw, geo.na, geo.nb + 1, 3, 3)
+    P = {s: torch.empty(shape, dtype=torch.complex128, device="cuda") for s in ("gt", "lt")}
+
+    def step():
+        plan.pi(inst["G_gt"], inst["G_lt"], P["gt"], P["lt"], stream=stream)
+
+    steps, warm = 3, 1
+    per, clk = leg_timing(step, steps, warm, stream, uuid)
+    plan.status()
+    ms = statistics.mean(per)
+    flops = 2 * pi_flops(geo, inst["neigh"].cpu().numpy())
+    achieved = flops / (ms / 1e3) / 1e12
+    res = {"workload": "Pi (Eqs. 4-5), FP64: Nkz=Nqz=5, NE=256, Nw=32, Na=152, Nb=4 chain, complex128, seed 5",
+           "value": geo.nqz * geo.nw * geo.na / (ms / 1e3), "unit": "(qz, w, atom) points/s",
+           "ms_per_step": ms, "p50_ms": pct(per, 50), "steps": steps, "warmup": warm,
+           "gpu_launches": steps + warm, "clocks": clk,
+           "roofline": {"bound": "alu", "kernel": "sse_pi_kernel", "achieved": achieved,
+                        "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                        "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (not measured)",
+                        "algorithmic_flops_per_launch": flops}}
+    plan.close()
+    del inst, P
     torch.cuda.empty_cache()
     return res
 

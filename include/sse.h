@@ -213,7 +213,7 @@ SSE_API sse_status sse_batch_tuning(sse_plan_t *const *plans, const sse_io *ios,
 typedef struct {
     sse_status status;    /* final status once sse_poll stops returning SSE_NOT_READY */
     double t_submit_ms;   /* host steady-clock times (milliseconds) */
-    double t_start_ms;    /* when its round was launched (0 while pending) */
+    double t_start_ms;    /* when its round's kernels had been enqueued (0 before) */
     double t_end_ms;      /* when the server saw its round complete (or cancelled it) */
     int32_t round_size;   /* requests in the round it ran in */
 } sse_result;

@@ -162,14 +162,12 @@ void launch_round(sse_server_s *s, std::unique_lock<std::mutex> &lock, std::vect
     Round r;
     r.slot = si;
     r.tickets = group;
-    const double t_launch = now_ms();
     std::vector<Plan *> plans;
     std::vector<double> slots_per_atom;
     std::vector<sse_io> ios;
     for (uint64_t tk : group) {
         Request &q = s->reqs[tk];
         q.state = kRunning;
-        q.t_start = t_launch;
         q.round_size = (int)group.size();
         plans.push_back(plan_core(q.plan));
         slots_per_atom.push_back(plan_slots_per_atom(q.plan));
@@ -190,6 +188,10 @@ void launch_round(sse_server_s *s, std::unique_lock<std::mutex> &lock, std::vect
         if (e != cudaSuccess) rs = cuda_fail(e, "record the round's completion");
     }
     lock.lock();
+    // t_start: the round's kernels are enqueued (set only now, so a caller that sees it knows
+    // the launch has been issued)
+    const double t_launched = now_ms();
+    for (uint64_t tk : group) s->reqs[tk].t_start = t_launched;
     if (rs != SSE_OK) {
         finish_round(s, r, rs);
         return;
