@@ -152,6 +152,38 @@ __device__ __forceinline__ uint2 split2_bf16(float a, float b) {
     return make_uint2(*reinterpret_cast<const uint32_t *>(&h), *reinterpret_cast<const uint32_t *>(&l));
 }
 
+// Split products folded into K (Nkz <= 3, where a K row (i, k') holds L = 3 Nkz <= 9 values):
+// the row x becomes [hi(x) | hi(x) | lo(x) | 0] on one side of the MMA and [hi | lo | hi | 0]
+// on the other, so that one K = 32 contraction gives hi.hi + hi.lo + lo.hi.  `first_hi`
+// selects the [hi | hi | lo] order (the Toeplitz operand); otherwise [hi | lo | hi] (X).
+// Returns the 32 bf16 values packed in pairs, the first in the low half of each word.
+template <int L>
+__device__ __forceinline__ void splitk_row(const float *x, bool first_hi, uint32_t (&w)[16]) {
+    static_assert(3 * L <= 32, "split-in-K row");
+    uint32_t h[L], l[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(x[i]);
+        const __nv_bfloat16 lb = __float2bfloat16_rn(x[i] - __bfloat162float(hb));
+        h[i] = __bfloat16_as_ushort(hb);
+        l[i] = __bfloat16_as_ushort(lb);
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        uint32_t pair = 0;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int kk = 2 * m + half, seg = kk / L, idx = kk % L;
+            uint32_t v = 0;
+            if (seg == 0) v = h[idx];
+            else if (seg == 1) v = first_hi ? h[idx] : l[idx];
+            else if (seg == 2) v = first_hi ? l[idx] : h[idx];
+            pair |= v << (16 * half);
+        }
+        w[m] = pair;
+    }
+}
+
 // Each word holds a (re-part, im-part) K pair (Re T, -Im T); the imaginary-part accumulator
 // needs (Im T, Re T): swap the halves and flip the sign of the new low half.
 __device__ __forceinline__ uint32_t to_im_pair(uint32_t w) { return __byte_perm(w, 0u, 0x1032) ^ 0x00008000u; }
@@ -933,8 +965,34 @@ __global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restri
     }
     __syncthreads();
     // direct table: [q = Re, Im][hi, lo][group (k, j)][K group][row r] x 16 bytes, entry
-    // (i, k') of row r = Re or Im of Df_ij[(k - k') mod Nkz][r - (TE - 1)]
-    const int nitems = 2 * GG::DA_GROUPS * 2 * da_rows;
+    // (i, k') of row r = Re or Im of Df_ij[(k - k') mod Nkz][r - (TE - 1)]; at Nkz <= 3
+    // [q][group][K group 0..3][row r] with the split products in K: (hi | hi | lo) of the entries
+    if constexpr (NK <= 3) {
+        constexpr int L = 3 * NK;
+        const int nrow = 2 * GG::DA_GROUPS * da_rows;
+        for (int x = tid; x < nrow; x += 256) {
+            const int r = x % da_rows, gq = (x / da_rows) % GG::DA_GROUPS, q = x / (da_rows * GG::DA_GROUPS);
+            const int k = gq / 3, j = gq % 3, w0 = r - (GG::DA_TE - 1);
+            float v[L];
+#pragma unroll
+            for (int kk = 0; kk < L; ++kk) {
+                float val = 0.f;
+                if (gq < 3 * NK && w0 >= 0 && w0 < nw) {
+                    const int i = kk / NK, kp = kk % NK;
+                    const float2 T = dfold[(((k - kp + NK) % NK) * nw + w0) * 9 + i * 3 + j];
+                    val = q ? T.y : T.x;
+                }
+                v[kk] = val;
+            }
+            uint32_t wv[16];
+            splitk_row<L>(v, true, wv);
+#pragma unroll
+            for (int kg = 0; kg < 4; ++kg)
+                *(uint4 *)(tab + ((((size_t)q * GG::DA_GROUPS + gq) * 4 + kg) * da_rows + r) * 16) =
+                    make_uint4(wv[4 * kg], wv[4 * kg + 1], wv[4 * kg + 2], wv[4 * kg + 3]);
+        }
+    }
+    const int nitems = NK <= 3 ? 0 : 2 * GG::DA_GROUPS * 2 * da_rows;
     for (int x = tid; x < nitems; x += 256) {
         const int r = x % da_rows, kg = (x / da_rows) % 2, gq = (x / (2 * da_rows)) % GG::DA_GROUPS;
         const int q = x / (2 * da_rows * GG::DA_GROUPS);
@@ -1029,6 +1087,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     // encode them for the pre-product; it needs every accumulator and post-product row in
     // lane quarters 0-2, so that those warps never take part in the epilogue.
     static_assert(!ENC || (kVRows <= 96 && kPostRows <= 96), "encoding form: rows in lane quarters 0-2");
+    // At Nkz <= 3 the split products are folded into K (K row (i, k') = 3 Nkz <= 9 values):
+    // B planes [Re X, Im X] of K = 32 and two MMAs per complex term instead of three.
+    constexpr bool SPLITK = NK <= 3;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ctl = warp == kTcCtlWarp || warp == kTcCtl2Warp || warp == kTcPreWarp;  // MMA-issuing warps
@@ -1217,14 +1278,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 Pos m{t_begin, 0, 0};
                 constexpr uint32_t idesc = idesc_bf16_f32(kRowsMax, kCh);
                 constexpr uint32_t idesc_negb = idesc | (1u << 14);
-                const uint32_t lbo_a = (uint32_t)da_rows * 16, sbo_a = 2u * lbo_a;
+                const uint32_t lbo_a = (uint32_t)da_rows * 16, sbo_a = (SPLITK ? 4u : 2u) * lbo_a;
                 const uint32_t tstride = (uint32_t)GG::DA_GROUPS * 2 * da_rows * 16;
                 // A (direct table) at row 0 for (re/im, hi/lo); stage st starts at row nw - 1 - st + TE - 1
+                // (split-in-K form: ta[0] = the Re table, ta[2] = the Im table, two K chunks each)
                 uint64_t ta[4];
 #pragma unroll
                 for (int x = 0; x < 4; ++x) ta[x] = smem_desc(smem_u32(sTab) + (uint32_t)x * tstride, lbo_a, sbo_a);
                 // B (X of the stage) of B stage 0; stage 1 is kBufStep further, planes kPlaneStep apart
-                const uint64_t tb0 = smem_desc(smem_u32(sB), 128, GG::DA_SBO_B);
+                const uint64_t tb0 = smem_desc(smem_u32(sB), 128, SPLITK ? 2 * GG::DA_SBO_B : GG::DA_SBO_B);
                 constexpr uint64_t kPlaneStep = GG::DA_B_PLANE >> 4, kBufStep = (4 * GG::DA_B_PLANE) >> 4;
                 const uint64_t pp_ah = smem_desc(smem_u32(sApost), 128, kPostSbo);
                 const uint64_t pp_al = smem_desc(smem_u32(sApost) + kPostAPlane, 128, kPostSbo);
@@ -1265,7 +1327,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const uint64_t bre_h = b0, bre_l = b0 + kPlaneStep, bim_h = b0 + 2 * kPlaneStep, bim_l = b0 + 3 * kPlaneStep;
                     const uint32_t dre = tmem, dim = tmem + kTcAccIm;
                     const uint32_t acc0 = job_first ? 0u : 1u;
-                    if (re_side) {
+                    if constexpr (SPLITK) {
+                        // planes [Re X | Im X] (K = 32 each) and tables [Re T | Im T] (K = 32 each)
+                        const uint64_t a_k1 = (uint64_t)((2u * lbo_a) >> 4), b_k1 = 256 >> 4;
+                        const uint64_t br = b0, bi = b0 + 2 * kPlaneStep;
+                        if (re_side) {
+                            // Re V = Re T Re X - Im T Im X
+                            mma_ss(dre, are_h, br, idesc, acc0);
+                            mma_ss(dre, are_h + a_k1, br + b_k1, idesc, 1u);
+                            mma_ss(dre, aim_h, bi, idesc_negb, 1u);
+                            mma_ss(dre, aim_h + a_k1, bi + b_k1, idesc_negb, 1u);
+                        } else {
+                            // Im V = Im T Re X + Re T Im X
+                            mma_ss(dim, aim_h, br, idesc, acc0);
+                            mma_ss(dim, aim_h + a_k1, br + b_k1, idesc, 1u);
+                            mma_ss(dim, are_h, bi, idesc, 1u);
+                            mma_ss(dim, are_h + a_k1, bi + b_k1, idesc, 1u);
+                        }
+                    } else if (re_side) {
                         // Re V = Re T Re X - Im T Im X
                         mma_ss(dre, are_h, bre_h, idesc, acc0);
                         mma_ss(dre, are_h, bre_l, idesc, 1u);
@@ -1562,12 +1641,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         lv[x] = hl.y;
                     }
                     const int pr = lane >> 4, n = (4 * q4 + ((lane >> 2) & 3)) * 12 + 4 * cb + (lane & 3);
-                    uint8_t *ph = sB + sb * (4 * GG::DA_B_PLANE) + (2 * pr) * GG::DA_B_PLANE + (n >> 3) * GG::DA_SBO_B +
-                                  (n & 7) * 16;
-                    *(uint4 *)ph = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                    *(uint4 *)(ph + 128) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
-                    *(uint4 *)(ph + GG::DA_B_PLANE) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-                    *(uint4 *)(ph + GG::DA_B_PLANE + 128) = make_uint4(lv[4], lv[5], lv[6], lv[7]);
+                    if constexpr (SPLITK) {
+                        // plane pr of K = 32: (hi | lo | hi) of the row, four 16-byte core-matrix rows
+                        uint32_t wv[16];
+                        splitk_row<3 * NK>(v, false, wv);
+                        uint8_t *ph = sB + sb * (4 * GG::DA_B_PLANE) + (2 * pr) * GG::DA_B_PLANE + (n >> 3) * (2 * GG::DA_SBO_B) +
+                                      (n & 7) * 16;
+#pragma unroll
+                        for (int kg = 0; kg < 4; ++kg)
+                            *(uint4 *)(ph + kg * 128) = make_uint4(wv[4 * kg], wv[4 * kg + 1], wv[4 * kg + 2], wv[4 * kg + 3]);
+                    } else {
+                        uint8_t *ph = sB + sb * (4 * GG::DA_B_PLANE) + (2 * pr) * GG::DA_B_PLANE + (n >> 3) * GG::DA_SBO_B +
+                                      (n & 7) * 16;
+                        *(uint4 *)ph = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *(uint4 *)(ph + 128) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
+                        *(uint4 *)(ph + GG::DA_B_PLANE) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                        *(uint4 *)(ph + GG::DA_B_PLANE + 128) = make_uint4(lv[4], lv[5], lv[6], lv[7]);
+                    }
                 }
                 if (xw) {
                     fence_proxy_async_smem();
