@@ -1092,11 +1092,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     constexpr bool SPLITK = NK <= 3;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool ctl = warp == kTcCtlWarp || warp == kTcCtl2Warp || warp == kTcPreWarp;  // MMA-issuing warps
-    const bool re_side = warp == kTcCtlWarp;   // main MMAs into Re V, the post-product
+    // Roles.  The encoding form's encoders are the warps of lane quarter 3, which share SM
+    // sub-partition 3 (warp % 4) with warp 15; there the Re-side issuer moves to warp 13 and
+    // the (light) bulk-copy lane to warp 15, so that no issuer shares a scheduler with them.
+    constexpr int kCtlWarp = ENC ? kTcPrdWarp : kTcCtlWarp, kPrdWarp = ENC ? kTcCtlWarp : kTcPrdWarp;
+    const bool ctl = warp == kCtlWarp || warp == kTcCtl2Warp || warp == kTcPreWarp;  // MMA-issuing warps
+    const bool re_side = warp == kCtlWarp;     // main MMAs into Re V, the post-product
     const bool im_side = warp == kTcCtl2Warp;  // main MMAs into Im V
     const bool pre_side = warp == kTcPreWarp;  // the pre-product
-    const bool prd = warp == kTcPrdWarp;                          // bulk-copy warp
+    const bool prd = warp == kPrdWarp;         // bulk-copy warp
     const int nw = prm.nw;
     const int omega_max = prm.omega_first + nw - 1;
     const int da_rows = nw + 2 * GG::DA_TE - 2;
@@ -1166,6 +1170,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (warp == 0) {
         tmem_alloc(s_tmem, kTmemCols);
         tmem_relinquish();
+    }
+    if (ENC && (warp & 3) == 3 && warp < kTcBuilders / 32) {
+        // the encoders write only the live part of the ring's slices (rows below 12 Nkz, K below
+        // 24); the rest stays zero from here on
+        for (int x = (warp >> 2) * 32 + lane; x < kTcRing * kTcPairBytes / 16; x += kTcEncoders)
+            *(uint4 *)(sRing + (size_t)x * 16) = make_uint4(0u, 0u, 0u, 0u);
+        fence_proxy_async_smem();
     }
     tc_fence_before();
     __syncthreads();
@@ -1497,6 +1508,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             // blocks and for the ring slot's previous pre-product, then write the slices -- rows
             // n' = (t / 4) 4 Nkz + k' 4 + t % 4 (12 Nkz used of 64), K = (re/im of G, u) (24 of
             // 32), bf16 hi then lo plane, core-matrix order -- and hand the slot to the pre-product.
+            // One thread per live row (stage h, n'): the row's K values are the column t of the
+            // block G[k'] (twelve u, re then im).
             const int et = (warp >> 2) * 32 + lane;  // 0 .. 95
             const int slot_len = (t_end - t_begin) * prm.nst;
             const int npairs = (slot_len + 1) / 2;
@@ -1508,38 +1521,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     if (!(ok = mbar_wait_bounded_sleep(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
                     const uint8_t *raw = sRaw + (size_t)slot * 2 * NK * kCh * sizeof(CT);
                     uint8_t *dst = sRing + slot * kTcPairBytes;
-                    for (int it = et; it < 2 * 64 * 4; it += kTcEncoders) {  // (stage h, row n', K group)
-                        const int h = it >> 8, np = (it >> 2) & 63, kg = it & 3;
+                    for (int it = et; it < 2 * 12 * NK; it += kTcEncoders) {  // (stage h, live row n')
+                        const int h = it / (12 * NK), np = it % (12 * NK);
                         const int o2 = 2 * pr + h;
-                        bool live = np < 12 * NK && o2 < slot_len;
+                        bool live = o2 < slot_len;
                         if (live) {
                             const int t = t_begin + o2 / prm.nst, st = o2 % prm.nst;
                             const int Ep = t * TE - omega_max + st;
                             live = Ep >= 0 && Ep < d.ne;
                         }
-                        float v[8];
+                        const int blk = np / (4 * NK), kp = (np % (4 * NK)) / 4, t = 4 * blk + np % 4;
+                        const CT *col = (const CT *)raw + (h * NK + kp) * kCh + t;
+                        float v[24];  // K = u (re), 12 + u (im)
 #pragma unroll
-                        for (int xx = 0; xx < 8; ++xx) {
-                            const int kk = kg * 8 + xx;
-                            float val = 0.f;
-                            if (live && kk < 24) {
-                                const int blk = np / (4 * NK), kp = (np % (4 * NK)) / 4, t = 4 * blk + np % 4;
-                                const int pc = kk / 12, u = kk % 12;
-                                const float2 c = load_c32_smem((const CT *)raw + (h * NK + kp) * kCh + u * 12 + t);
-                                val = pc ? c.y : c.x;
+                        for (int u = 0; u < 12; ++u) {
+                            const float2 c = live ? load_c32_smem(col + u * 12) : make_float2(0.f, 0.f);
+                            v[u] = c.x;
+                            v[12 + u] = c.y;
+                        }
+                        uint8_t *pd = dst + h * 4096 + (np >> 3) * 512 + (np & 7) * 16;
+#pragma unroll
+                        for (int kg = 0; kg < 3; ++kg) {
+                            uint32_t hv[4], lv[4];
+#pragma unroll
+                            for (int xx = 0; xx < 4; ++xx) {
+                                const uint2 hl = split2_bf16(v[8 * kg + 2 * xx], v[8 * kg + 2 * xx + 1]);
+                                hv[xx] = hl.x;
+                                lv[xx] = hl.y;
                             }
-                            v[xx] = val;
+                            *(uint4 *)(pd + kg * 128) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                            *(uint4 *)(pd + 8192 + kg * 128) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                         }
-                        uint32_t hv[4], lv[4];
-#pragma unroll
-                        for (int xx = 0; xx < 4; ++xx) {
-                            const uint2 hl = split2_bf16(v[2 * xx], v[2 * xx + 1]);
-                            hv[xx] = hl.x;
-                            lv[xx] = hl.y;
-                        }
-                        uint8_t *pd = dst + h * 4096 + (np >> 3) * 512 + kg * 128 + (np & 7) * 16;
-                        *(uint4 *)pd = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *(uint4 *)(pd + 8192) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
                     fence_proxy_async_smem();
                     mbar_arrive(&bar_rawfree[slot]);
