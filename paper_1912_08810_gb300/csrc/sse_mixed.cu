@@ -1127,8 +1127,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bar_tab = bar_slotfree + 1;            // the slot's direct table copied in
     uint64_t *bar_enc = bar_tab + 1;                 // [kTcRing] encoding form: a pair encoded into the ring
     uint64_t *bar_rawfree = bar_enc + kTcRing;       // [kTcRing] encoding form: a raw pair consumed
-    uint32_t *s_tmem = (uint32_t *)(bar_rawfree + kTcRing);
-    static_assert((4 * kTcRing + 2 * kTcBStages + 9) * 8 + 7 * 4 <= kTcBarBytes, "barrier area");
+    uint64_t *bar_xfree = bar_rawfree + kTcRing;     // the builders have read X of a pair (TMEM free)
+    uint32_t *s_tmem = (uint32_t *)(bar_xfree + 1);
+    static_assert((4 * kTcRing + 2 * kTcBStages + 10) * 8 + 7 * 4 <= kTcBarBytes, "barrier area");
     // abort flags, each written only by its role (builders: s_abort[0]) before the unit's
     // closing barrier and read by every thread after it
     int *s_abort = (int *)(s_tmem + 1);          // [2]
@@ -1153,6 +1154,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
         mbar_init(bar_slotfree, 3);  // the three issuing warps
         mbar_init(bar_fin, 3);       // the three issuing warps
         mbar_init(bar_apost, ENC ? kTcBuilders - kTcEncoders : kTcBuilders);
+        mbar_init(bar_xfree, kTcXBuilders);
         mbar_init(&bar_post[0], 1);
         mbar_init(&bar_post[1], 1);
         for (int b = 0; b < kTcRing; ++b) {
@@ -1305,16 +1307,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                 const uint64_t pp_bl = smem_desc(smem_u32(sBpost) + kPostBPlane, 128, kPostSbo);
                 const int slot_len = (t_end - t_begin) * prm.nst;  // stages of one slot in this unit
                 bool ok = true;
+                if (pre_side) {
+                    // the pre-product, pair by pair: the next pair's X goes into TMEM as soon as
+                    // the builders have read the previous one, ahead of the stages that use it
+                    const int npairs = (slot_len + 1) / 2;
+                    for (int vs = 0; vs < nvalid && ok; ++vs) {
+                        // the slot's pre-product operand copied in
+                        if (!(ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs))) break;
+                        ++slot_ctr;
+                        tc_fence_after();
+                        for (int pr = 0; pr < npairs && ok; ++pr) {
+                            if (pair_ctr > 0 && !(ok = mbar_wait_bounded(bar_xfree, (pair_ctr - 1) & 1, kWaitNs))) break;
+                            tc_fence_after();
+                            ok = premma();
+                        }
+                        if (ok) mma_commit(bar_slotfree);  // its pre-products of the slot
+                    }
+                }
                 int o = 0;  // stage index within the slot
-                for (int g = 0; g < total; ++g, advance(m), o = (o + 1 == slot_len) ? 0 : o + 1) {
+                for (int g = 0; g < (pre_side ? 0 : total); ++g, advance(m), o = (o + 1 == slot_len) ? 0 : o + 1) {
                     const int gg = g_base + g;
                     const bool job_first = m.st == 0, job_last = m.st == prm.nst - 1;
                     const int slot_rem = slot_len - 1 - o;  // stages after this one in its slot
-                    if (o == 0 && !im_side) {
-                        // the slot's pre-product operand (pre side) and post-product operand (Re side)
+                    if (o == 0 && re_side) {
+                        // the slot's post-product operand
                         if (!(ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs))) break;
                         tc_fence_after();
-                        if (pre_side && !(ok = premma())) break;
                     }
                     const int bb = gg % kTcBStages, use = gg / kTcBStages;  // B buffer and its use count
                     if (!(ok = mbar_wait_bounded(&bar_bready[bb], use & 1, kWaitNs))) break;
@@ -1324,13 +1342,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         if (!ok) break;
                     }
                     tc_fence_after();
-                    // X of the next pair ahead of this stage's main MMAs: the builders drained the
-                    // TMEM buffer at this (first) stage of the current pair
-                    if (pre_side) {
-                        if ((o & 1) == 0 && slot_rem >= 2 && !(ok = premma())) break;
-                        if (job_last && slot_rem == 0) mma_commit(bar_slotfree);  // its pre-products of the slot
-                        continue;
-                    }
                     const uint64_t r_start = (uint64_t)(nw - 1 - m.st + GG::DA_TE - 1);
                     const uint64_t are_h = ta[0] + r_start, are_l = ta[1] + r_start;
                     const uint64_t aim_h = ta[2] + r_start, aim_l = ta[3] + r_start;
@@ -1617,6 +1628,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         tmem_ld16x128_reps<NK>(ta + 64 + (16u << 16), nb);
                         tmem_ld_wait();
                         tc_fence_before();
+                        mbar_arrive(bar_xfree);  // the pre-product of the next pair may overwrite X
 #pragma unroll
                         for (int k = 0; k < NK; ++k) {
                             xnext[k] = na[2 * k];
