@@ -94,10 +94,12 @@ sse_fp64_direct_kernel(const int32_t *__restrict__ neigh, const CT *__restrict__
                 if (kk < 0) kk += d.nkz;
                 const CT *gq = G + ((size_t)kk * d.ne) * d.na * kBlk + (size_t)f * kBlk + c;
                 const CT *dq = D + (((size_t)q * d.nw) * d.na + a) * d.nb * 9 + (size_t)slot * 9;
-                for (int w = 0; w < d.nw; ++w) {
+                // frequencies whose E' = E - w - omega_first lies on the grid: w_lo drops E' above
+                // it (negative omega_first), w_hi those below it
+                const int w_lo = max(0, e - d.omega_first - (d.ne - 1));
+                const int w_hi = min(d.nw - 1, e - d.omega_first);
+                for (int w = w_lo; w <= w_hi; ++w) {
                     const int ep = e - w - d.omega_first;
-                    if (ep < 0) break;         // every later w is further below the grid
-                    if (ep >= d.ne) continue;  // E + |omega| above the grid (negative omega_first)
                     const CT *gp = gq + (size_t)ep * d.na * kBlk;
                     const CT *dw = dq + (size_t)w * d.na * d.nb * 9;
                     if (!SSE_BC(gp - G, (long long)d.nkz * d.ne * d.na * kBlk, status) ||
