@@ -101,6 +101,7 @@ struct MixParams {
     int32_t inject;         // failure-injection test hook (sse_debug_inject): skip one copy per CTA
     long long total_units;
     uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, off_x, off_bp, g_stage;
+    int32_t nbst;           // warp-specialised form: B buffers in flight (2 or 3)
     InstDesc inst[kMaxInst];
 };
 
@@ -799,6 +800,7 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
                     float v[8];
                     tmem_ld8(taddr + c0, v);
                     tmem_ld_wait();
+                    tmem_pin(v);
 #pragma unroll
                     for (int x = 0; x < 8; ++x) vrow[c0 + x] = v[x];
                 }
@@ -898,6 +900,7 @@ constexpr int kTcPreWarp = 12;              // the pre-product
 constexpr int kTcThreads = 512;
 constexpr int kTcRing = 2;   // pairs of G slices in flight
 constexpr int kTcBStages = 2;  // B operands in flight: builders build stage g + 1 while the MMAs of stage g run
+constexpr int kTcBStagesMax = 3;  // the encoding form takes a third where shared memory allows
 constexpr uint32_t kTcPairBytes = 16384;  // one ring slot: two slices, [hi s0 | hi s1 | lo s0 | lo s1]
 // TMEM columns of the warp-specialised kernel
 constexpr uint32_t kTcAccIm = 160;             // Im V (Re V at 0), 144 columns each
@@ -1076,7 +1079,7 @@ __global__ void __launch_bounds__(256) sse_slot_tables_kernel(const CT *__restri
     }
 }
 
-template <int NK, typename CT, bool ENC>
+template <int NK, typename CT, bool ENC, int BST>
 __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_constant__ MixParams prm) {
     using GG = Geo<NK>;
     constexpr int TE = GG::DA_TE;        // energies per tile of this form (rows (k, j, e): 3 NK TE)
@@ -1115,9 +1118,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bars = (uint64_t *)(smem + prm.off_bar);
     uint64_t *bar_g = bars;                          // [kTcRing] pair of slices landed
     uint64_t *bar_empty = bar_g + kTcRing;           // [kTcRing] pre-product done with a ring slot
-    uint64_t *bar_bready = bar_empty + kTcRing;      // [kTcBStages] B of a stage built
-    uint64_t *bar_mma = bar_bready + kTcBStages;     // [kTcBStages] main MMAs of a stage done (B free)
-    uint64_t *bar_post = bar_mma + kTcBStages;       // [2] post-product MMAs of a tile done
+    uint64_t *bar_bready = bar_empty + kTcRing;      // [nbst] B of a stage built
+    uint64_t *bar_mma = bar_bready + kTcBStagesMax;  // [nbst] main MMAs of a stage done (B free)
+    uint64_t *bar_post = bar_mma + kTcBStagesMax;    // [2] post-product MMAs of a tile done
     uint64_t *bar_pre = bar_post + 2;                // pre-product of a pair done
     uint64_t *bar_job = bar_pre + 1;                 // last MMAs of a job done
     uint64_t *bar_slot = bar_job + 1;                // the slot's pre- and post-product operands copied in
@@ -1129,7 +1132,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint64_t *bar_rawfree = bar_enc + kTcRing;       // [kTcRing] encoding form: a raw pair consumed
     uint64_t *bar_xfree = bar_rawfree + kTcRing;     // the builders have read X of a pair (TMEM free)
     uint32_t *s_tmem = (uint32_t *)(bar_xfree + 1);
-    static_assert((4 * kTcRing + 2 * kTcBStages + 10) * 8 + 7 * 4 <= kTcBarBytes, "barrier area");
+    static_assert((4 * kTcRing + 2 * kTcBStagesMax + 10) * 8 + 7 * 4 <= kTcBarBytes, "barrier area");
+    constexpr int nbst = BST;  // B buffers in flight (2, or 3 in the encoding form where they fit)
     // abort flags, each written only by its role (builders: s_abort[0]) before the unit's
     // closing barrier and read by every thread after it
     int *s_abort = (int *)(s_tmem + 1);          // [2]
@@ -1144,7 +1148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     if (tid == 0) {
         for (int b = 0; b < kTcRing; ++b) mbar_init(&bar_g[b], 1);
         mbar_init(bar_pre, 1);
-        for (int b = 0; b < kTcBStages; ++b) {
+        for (int b = 0; b < nbst; ++b) {
             mbar_init(&bar_bready[b], kTcXBuilders);
             mbar_init(&bar_mma[b], 2);  // a commit from each issuing warp
         }
@@ -1334,7 +1338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         if (!(ok = mbar_wait_bounded(bar_slot, slot_ctr & 1, kWaitNs))) break;
                         tc_fence_after();
                     }
-                    const int bb = gg % kTcBStages, use = gg / kTcBStages;  // B buffer and its use count
+                    const int bb = gg % nbst, use = gg / nbst;  // B buffer and its use count
                     if (!(ok = mbar_wait_bounded(&bar_bready[bb], use & 1, kWaitNs))) break;
                     if (o == 0) {
                         ok = mbar_wait_bounded(bar_tab, slot_ctr & 1, kWaitNs);
@@ -1528,8 +1532,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             for (int vs = 0; vs < nvalid && ok; ++vs)
                 for (int pr = 0; pr < npairs && ok; ++pr, ++pair_ctr) {
                     const int slot = pair_ctr % kTcRing, use = pair_ctr / kTcRing;
-                    if (!(ok = mbar_wait_bounded_sleep(&bar_g[slot], use & 1, kWaitNs))) break;
-                    if (!(ok = mbar_wait_bounded_sleep(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
+                    if (!(ok = mbar_wait_bounded(&bar_g[slot], use & 1, kWaitNs))) break;
+                    if (!(ok = mbar_wait_bounded(&bar_empty[slot], (use & 1) ^ 1, kWaitNs))) break;
                     const uint8_t *raw = sRaw + (size_t)slot * 2 * NK * kCh * sizeof(CT);
                     uint8_t *dst = sRing + slot * kTcPairBytes;
                     for (int it = et; it < 2 * 12 * NK; it += kTcEncoders) {  // (stage h, live row n')
@@ -1584,14 +1588,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             // leave the loop early, so every one reaches each builders_sync.
             bool bad = false;
             auto bwait = [&](uint64_t *bar, uint32_t parity) {
-                if (!bad && !mbar_wait_bounded_sleep(bar, parity, kWaitNs)) {
+                if (!bad && !mbar_wait_bounded(bar, parity, kWaitNs)) {
                     bad = true;
                     atomicOr(prm.status, kStatusTimeout);
                 }
             };
             for (int g = 0; g < total; ++g, advance(cur), o = (o + 1 == slot_len) ? 0 : o + 1) {
                 const int t = cur.t, vs = cur.vs, st = cur.st;
-                const int gg = g_base + g, sb = gg % kTcBStages, use = gg / kTcBStages;
+                const int gg = g_base + g, sb = gg % nbst, use = gg / nbst;
                 const int E0 = t * TE;
                 const bool job_first = st == 0, job_last = st == prm.nst - 1;
                 if (job_first && vs > 0 && (!ENC || xw)) {
@@ -1627,6 +1631,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         tmem_ld16x128_reps<NK>(ta + 64, na);
                         tmem_ld16x128_reps<NK>(ta + 64 + (16u << 16), nb);
                         tmem_ld_wait();
+                        tmem_pin(xa);
+                        tmem_pin(xb);
+                        tmem_pin(na);
+                        tmem_pin(nb);
                         tc_fence_before();
                         mbar_arrive(bar_xfree);  // the pre-product of the next pair may overwrite X
 #pragma unroll
@@ -1715,9 +1723,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         uint32_t vr[12], vi[12];
                         if (q < kPostTiles) {
                             const uint32_t ta = tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)((3 * q + arl) * 12);
-                            tmem_ld8(ta, *reinterpret_cast<float(*)[8]>(vr));
+                            tmem_ld8(ta, *reinterpret_cast<uint32_t(*)[8]>(vr));
                             tmem_ld4(ta + 8, *reinterpret_cast<uint32_t(*)[4]>(vr + 8));
-                            tmem_ld8(ta + kTcAccIm, *reinterpret_cast<float(*)[8]>(vi));
+                            tmem_ld8(ta + kTcAccIm, *reinterpret_cast<uint32_t(*)[8]>(vi));
                             tmem_ld4(ta + kTcAccIm + 8, *reinterpret_cast<uint32_t(*)[4]>(vi + 8));
                         }
                         if (q > 0) {
@@ -1726,6 +1734,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tc_fence_after();
                         }
                         tmem_ld_wait();
+                        if (q < kPostTiles) {
+                            tmem_pin(vr);
+                            tmem_pin(vi);
+                        }
                         if (q < kPostTiles && am < kVRows) {
                             // ---- A tile q: rows (r', e, k), K = (j, t, re/im), bf16 hi / lo ----
                             const int row = arl * (TE * NK) + ae * NK + ak;
@@ -1761,6 +1773,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tmem_ld8(tmem + ((uint32_t)(dq * 32) << 16) + (((tq - 1) & 1) ? kTcPost1 : kTcPost0) +
                                          (uint32_t)(8 * dsub), pv);
                             tmem_ld_wait();
+                            tmem_pin(pv);
                             tc_fence_before();
                         }
                         if (q > 0 && dlive && SSE_BC((dst - S) + 3, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) {
@@ -1814,7 +1827,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 // pre-product's dH operand, the direct table, the post-product's conj(dH) operand and the
 // barriers.
 template <int NK, bool ENC>
-uint32_t tc_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
+uint32_t tc_layout(const Dims &d, size_t cbytes, MixParams &prm, uint32_t bregion) {
     using GG = Geo<NK>;
     uint32_t off = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
@@ -1823,9 +1836,7 @@ uint32_t tc_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
         off += bytes;
         return at;
     };
-    const uint32_t bsz = kTcBStages * 4 * GG::DA_B_PLANE;
-    const uint32_t nv = 2 * kPostAPlane;
-    prm.off_b = take(bsz > nv ? bsz : nv, 1024);
+    prm.off_b = take(bregion, 1024);
     prm.off_g = take(kTcRing * kTcPairBytes, 1024);
     prm.off_x = ENC ? take((uint32_t)(kTcRing * 2 * NK * kCh * cbytes), 128) : 0;
     prm.off_a = take(2 * 8192, 1024);
@@ -1836,6 +1847,23 @@ uint32_t tc_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
     prm.off_bar = take(kTcBarBytes + 8 + 2 * kMaxSlots * 4, 8);
     prm.g_stage = 0;
     return off;
+}
+template <int NK, bool ENC>
+uint32_t tc_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
+    using GG = Geo<NK>;
+    // B buffers (the post-product A tile overlays them): a third one in the encoding form
+    // when the whole layout still fits
+    const uint32_t nv = 2 * kPostAPlane;
+    const uint32_t b2 = kTcBStages * 4 * GG::DA_B_PLANE, b3 = kTcBStagesMax * 4 * GG::DA_B_PLANE;
+    if (ENC) {
+        const uint32_t s3 = tc_layout<NK, ENC>(d, cbytes, prm, b3 > nv ? b3 : nv);
+        if (s3 <= 232448u) {
+            prm.nbst = kTcBStagesMax;
+            return s3;
+        }
+    }
+    prm.nbst = kTcBStages;
+    return tc_layout<NK, ENC>(d, cbytes, prm, b2 > nv ? b2 : nv);
 }
 
 template <int NK>
@@ -1920,6 +1948,22 @@ bool fill_inst(InstDesc &I, const Plan &p, const sse_io &io, int tpc, bool dfull
 
 long long inst_units(const InstDesc &I) { return (long long)I.nsign * I.na * I.nchunks; }
 
+// The warp-specialised kernel instance for a B-buffer count (three only in the encoding
+// form), and its launch with the count tc_smem_bytes chose.
+template <int NK, typename CT, bool ENC, int BST>
+auto tc_kernel_of() {
+    if constexpr (BST == kTcBStagesMax && !ENC) return sse_tc_kernel<NK, CT, ENC, kTcBStages>;
+    else return sse_tc_kernel<NK, CT, ENC, BST>;
+}
+template <int NK, typename CT>
+void launch_tc(const MixParams &prm, unsigned grid, uint32_t smem, cudaStream_t st) {
+    constexpr bool ENC = NK < 5;
+    if (ENC && prm.nbst == kTcBStagesMax)
+        tc_kernel_of<NK, CT, ENC, kTcBStagesMax>()<<<grid, kTcThreads, smem, st>>>(prm);
+    else
+        tc_kernel_of<NK, CT, ENC, kTcBStages>()<<<grid, kTcThreads, smem, st>>>(prm);
+}
+
 template <int NK, typename CT, bool V3>
 sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *status) {
     using GG = Geo<NK>;
@@ -1936,7 +1980,9 @@ sse_status prepare(MixParams &prm, uint32_t &smem, const Dims &d, int32_t *statu
     prm.nst = V3 ? GG::DA_TE + d.nw - 1 : (GG::TE + d.nw - 1 + GG::P - 1) / GG::P;
     cudaError_t e;
     if constexpr (V3)
-        e = cudaFuncSetAttribute(sse_tc_kernel<NK, CT, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = prm.nbst == kTcBStagesMax
+                ? cudaFuncSetAttribute(tc_kernel_of<NK, CT, ENC, kTcBStagesMax>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                : cudaFuncSetAttribute(tc_kernel_of<NK, CT, ENC, kTcBStages>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else
         e = cudaFuncSetAttribute(sse_mixed_kernel<NK, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
@@ -2018,7 +2064,7 @@ sse_status launch_nk(Plan &p, const sse_io &io, cudaStream_t st, bool dfull) {
     }
     timing_mark(p, ts, 1, st);
     if constexpr (V3)
-        sse_tc_kernel<NK, CT, (NK < 5)><<<(unsigned)prm.total_units, kTcThreads, smem, st>>>(prm);
+        launch_tc<NK, CT>(prm, (unsigned)prm.total_units, smem, st);
     else
         sse_mixed_kernel<NK, CT><<<(unsigned)prm.total_units, kThreads, smem, st>>>(prm);
     timing_mark(p, ts, 2, st);
@@ -2063,7 +2109,7 @@ sse_status launch_batch_nk(Plan *const *plans, const sse_io *ios, const int *ord
         if (e != cudaSuccess) return cuda_fail(e, "reset the work counter");
         const long long grid = units < sms ? units : sms;
         if constexpr (V3)
-            sse_tc_kernel<NK, CT, (NK < 5)><<<(unsigned)grid, kTcThreads, smem, st>>>(prm);
+            launch_tc<NK, CT>(prm, (unsigned)grid, smem, st);
         else
             sse_mixed_kernel<NK, CT><<<(unsigned)grid, kThreads, smem, st>>>(prm);
         e = cudaGetLastError();

@@ -215,20 +215,17 @@ __device__ __forceinline__ void tmem_ld16x128_reps(uint32_t taddr, uint32_t (&r)
     if constexpr (NK == 1) tmem_ld16x128_x1(taddr, reinterpret_cast<R2>(r[0]));
 }
 
-// 32 lanes x 8 columns of 32-bit values: thread t of the warp gets lane (base + t).
+// 32 lanes x 8 columns of 32-bit values: thread t of the warp gets lane (base + t).  The
+// destinations are the caller's registers themselves (no copies before the wait).
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
                  : "r"(taddr));
-    v[0] = __uint_as_float(r0);
-    v[1] = __uint_as_float(r1);
-    v[2] = __uint_as_float(r2);
-    v[3] = __uint_as_float(r3);
-    v[4] = __uint_as_float(r4);
-    v[5] = __uint_as_float(r5);
-    v[6] = __uint_as_float(r6);
-    v[7] = __uint_as_float(r7);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 
 // 4 consecutive columns of the warp's 32 lanes; use the values only after tmem_ld_wait().
@@ -254,6 +251,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// tcgen05.ld fills its destination registers asynchronously: they hold the loaded values
+// only after tcgen05.wait::ld, which the compiler does not know.  Passing each loaded
+// register through an empty asm statement after the wait makes the compiler treat it as
+// written there, so that no use of it (nor a copy) is scheduled above the wait.
+template <int N>
+__device__ __forceinline__ void tmem_pin(uint32_t (&r)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
+}
+template <int N>
+__device__ __forceinline__ void tmem_pin(float (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+f"(v[i]));
+}
 
 // ---- number formats ---------------------------------------------------------------------
 
