@@ -171,15 +171,12 @@ def source_digest(paths):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_tag, digest):
-    """DRAM bytes per launch recorded in profiles/<kernel_tag>*.md for this exact source."""
-    pdir = os.path.join(ROOT, "profiles")
-    if not os.path.isdir(pdir):
-        return None
-    for fn in sorted(os.listdir(pdir)):
-        if not fn.startswith(kernel_tag) or not fn.endswith(".md"):
-            continue
-        txt = open(os.path.join(pdir, fn)).read()
+def profiled_traffic(kernel_tag, digest, workload):
+    """DRAM bytes per launch recorded in profiles/<kernel_tag>_<workload>.md for this exact
+    source."""
+    fn = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload}.md")
+    if os.path.exists(fn):
+        txt = open(fn).read()
         m_d = re.search(r"source_digest:\s*([0-9a-f]+)", txt)
         m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
         if m_d and m_t and m_d.group(1) == digest:
@@ -382,7 +379,7 @@ def run_ours(args):
     ws_form = form == "mixed" and info.workspace_bytes > (1 << 20)  # the warp-specialised form's workspace
     tag, srcs = KERNEL_SOURCES["mixed" if ws_form else ("mixed_single_role" if form == "mixed" else form)]
     digest = source_digest(srcs)
-    traffic = profiled_traffic(tag, digest)
+    traffic = profiled_traffic(tag, digest, name)
     if form == "mixed":
         peak, peak_src = tensor_peak(peaks, clk)
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": peak_src}
