@@ -102,6 +102,7 @@ struct MixParams {
     long long total_units;
     uint32_t off_b, off_a, off_g, off_df, off_dh, off_bar, off_x, off_bp, g_stage;
     int32_t nbst;           // warp-specialised form: B buffers in flight (2 or 3)
+    uint32_t off_stg;       // warp-specialised form, Nkz = 5: staged post-product results (0: none)
     InstDesc inst[kMaxInst];
 };
 
@@ -917,6 +918,10 @@ constexpr uint32_t kPostBPlane = (32 / 8) * kPostSbo;        // 5120
 constexpr int kTcBarBytes = 256;  // 24 mbarriers, the TMEM address and the flags; the unit index follows
 constexpr int kTcEncoders = 96;   // encoding form: the warps of TMEM lane quarter 3 (3, 7, 11)
 constexpr int kPostTiles = 4;     // post-product M tiles per job (three rows r of the block each)
+// Nkz = 5: the results of the job's last kStgTiles post-product tiles are staged in shared
+// memory (rows of kStgStride floats: 24 values and padding against bank conflicts) and
+// added to Sigma by the builder warps without stage work during the next job
+constexpr int kStgTiles = 2, kStgStride = 28;
 
 // dH_j[s, t] in shared memory: rows s in blocks of 4 with 4 float2 of padding between
 // blocks, so the epilogue's three row blocks read distinct banks.
@@ -1115,6 +1120,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     uint8_t *sRaw = smem + prm.off_x;            // encoding form: [kTcRing] pairs of raw G blocks
     uint8_t *sApre = smem + prm.off_a;           // pre-product A: dH operand [hi, lo]
     uint8_t *sTab = smem + prm.off_df;           // direct Toeplitz table of the slot
+    float *stg = (!ENC && prm.off_stg) ? (float *)(smem + prm.off_stg) : nullptr;  // [kStgTiles][kPostRows][kStgStride]
     uint64_t *bars = (uint64_t *)(smem + prm.off_bar);
     uint64_t *bar_g = bars;                          // [kTcRing] pair of slices landed
     uint64_t *bar_empty = bar_g + kTcRing;           // [kTcRing] pre-product done with a ring slot
@@ -1587,6 +1593,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
             // A failed wait marks this builder bad and skips its later waits; builders never
             // leave the loop early, so every one reaches each builders_sync.
             bool bad = false;
+            // Staged results of the previous job (Nkz = 5): its last kStgTiles post-product
+            // tiles, added to Sigma by the three warps without stage work (lane quarter 3)
+            // while this job runs.  Element (tile, row, s) always goes to the same thread, so
+            // the first slot's store and later slots' reductions to an address are ordered.
+            bool pend = false, pend_first = false;
+            int pend_E0 = 0;
+            auto flush = [&]() {
+                const int bt = (warp >> 2) * 32 + lane;  // 0 .. 95
+                for (int x = bt; x < kStgTiles * kPostRows * 12; x += 96) {
+                    const int c = x / (kStgTiles * kPostRows), rem = x % (kStgTiles * kPostRows);
+                    const int tl = rem / kPostRows, row = rem % kPostRows;
+                    const int srl = row / (TE * NK), se = (row / NK) % TE, sk = row % NK;
+                    if (pend_E0 + se >= d.ne) continue;
+                    const size_t idx = (((size_t)sk * d.ne + pend_E0 + se) * d.na + a) * kCh +
+                                       (3 * (kPostTiles - kStgTiles + tl) + srl) * 12 + c;
+                    if (!SSE_BC(idx, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) continue;
+                    const float *sp = stg + ((size_t)tl * kPostRows + row) * kStgStride + 2 * c;
+                    const float2 v = make_float2(sp[0], sp[1]);
+                    if (pend_first) S[idx] = final_of<CT>(v);
+                    else slot_add(S + idx, v);
+                }
+                pend = false;
+            };
             auto bwait = [&](uint64_t *bar, uint32_t parity) {
                 if (!bad && !mbar_wait_bounded(bar, parity, kWaitNs)) {
                     bad = true;
@@ -1609,6 +1638,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             prefetch_l2((const uint8_t *)(S + (((size_t)k * d.ne + E) * d.na + a) * kCh) + ln * 128);
                     }
                 }
+                if (stg && !xw && pend) flush();  // the previous job's staged tiles
 
                 // ---- X of this stage -> B buffer sb.  Warp (lane quarter q4 < 3, column block cb)
                 // loads rows (i = 0, 1) and (i = 2, zero) of the four r of its quarter, columns
@@ -1776,7 +1806,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tmem_pin(pv);
                             tc_fence_before();
                         }
-                        if (q > 0 && dlive && SSE_BC((dst - S) + 3, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) {
+                        if (q > 0 && stg && q - 1 >= kPostTiles - kStgTiles) {
+                            // staged: added to Sigma during the next job (see flush)
+                            if (drow < kPostRows) {
+                                float *sp = stg + ((size_t)(q - 1 - (kPostTiles - kStgTiles)) * kPostRows + drow) * kStgStride + 8 * dsub;
+                                *(float4 *)sp = make_float4(pv[0], pv[1], pv[2], pv[3]);
+                                *(float4 *)(sp + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
+                            }
+                        } else if (q > 0 && dlive && SSE_BC((dst - S) + 3, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) {
                             // the slot's FP32 contribution into Sigma: the first slot stores it, every
                             // later slot adds it with a fire-and-forget reduction at L2 (FP64 adds for
                             // complex128, the running sum then being FP64; FP32 adds for complex64)
@@ -1792,8 +1829,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                                   4 * dsub;
                     }
                     tile_ctr += kPostTiles;
+                    if (stg) {
+                        builders_sync<ENC>();  // the staged tiles are complete
+                        pend = true;
+                        pend_E0 = E0;
+                        pend_first = first_slot;
+                    }
                 }
             }
+            if (stg && !xw && pend) flush();  // the unit's last job
             if (bad) s_abort[0] = 1;  // read by every thread after the unit's closing barrier
         }
         g_base += total;
@@ -1827,7 +1871,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 // pre-product's dH operand, the direct table, the post-product's conj(dH) operand and the
 // barriers.
 template <int NK, bool ENC>
-uint32_t tc_layout(const Dims &d, size_t cbytes, MixParams &prm, uint32_t bregion) {
+uint32_t tc_layout(const Dims &d, size_t cbytes, MixParams &prm, uint32_t bregion, uint32_t stg_bytes) {
     using GG = Geo<NK>;
     uint32_t off = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
@@ -1845,6 +1889,7 @@ uint32_t tc_layout(const Dims &d, size_t cbytes, MixParams &prm, uint32_t bregio
     prm.off_dh = 0;
     prm.off_bp = take(2 * kPostBPlane, 1024);
     prm.off_bar = take(kTcBarBytes + 8 + 2 * kMaxSlots * 4, 8);
+    prm.off_stg = stg_bytes ? take(stg_bytes, 128) : 0u;
     prm.g_stage = 0;
     return off;
 }
@@ -1856,14 +1901,20 @@ uint32_t tc_smem_bytes(const Dims &d, size_t cbytes, MixParams &prm) {
     const uint32_t nv = 2 * kPostAPlane;
     const uint32_t b2 = kTcBStages * 4 * GG::DA_B_PLANE, b3 = kTcBStagesMax * 4 * GG::DA_B_PLANE;
     if (ENC) {
-        const uint32_t s3 = tc_layout<NK, ENC>(d, cbytes, prm, b3 > nv ? b3 : nv);
+        const uint32_t s3 = tc_layout<NK, ENC>(d, cbytes, prm, b3 > nv ? b3 : nv, 0u);
         if (s3 <= 232448u) {
             prm.nbst = kTcBStagesMax;
             return s3;
         }
     }
     prm.nbst = kTcBStages;
-    return tc_layout<NK, ENC>(d, cbytes, prm, b2 > nv ? b2 : nv);
+    if (!ENC) {
+        // the staging of the last post-product tiles, where it fits
+        const uint32_t sb = (uint32_t)(kStgTiles * 3 * GG::DA_TE * NK * kStgStride * 4);
+        const uint32_t ss = tc_layout<NK, ENC>(d, cbytes, prm, b2 > nv ? b2 : nv, sb);
+        if (ss <= 232448u) return ss;
+    }
+    return tc_layout<NK, ENC>(d, cbytes, prm, b2 > nv ? b2 : nv, 0u);
 }
 
 template <int NK>
