@@ -172,7 +172,11 @@ SSE_API sse_status sse_pi(sse_plan_t *plan, const void *G_gt, const void *G_lt, 
 
 /* Same computation with HOST buffers (pageable or pinned): copies the inputs to
  * plan-owned device staging on `stream`, runs, copies Sigma back and synchronises
- * the stream before returning.  Staging is allocated on first use and kept. */
+ * the stream before returning.  Staging is allocated on first use and kept.  With both
+ * signs requested, the second sign runs on a plan-owned second stream (created on first
+ * use) whose input copies follow the first sign's and whose kernels follow the first
+ * sign's kernels, so that with pinned host buffers the copies of one sign overlap the
+ * other's computation; the call returns after both. */
 SSE_API sse_status sse_execute_host(sse_plan_t *plan, const sse_io *host_io, void *stream);
 
 /* Batched form: evaluate n independent instances -- each with its own plan and

@@ -251,6 +251,12 @@ sse_status sse_plan_destroy(sse_plan_t *plan) {
     if (plan->d_rev) cudaFree(plan->d_rev);
     if (plan->dt_scratch) cudaFree(plan->dt_scratch);
     if (plan->staging) cudaFree(plan->staging);
+    if (plan->side) {
+        cudaStreamSynchronize(plan->side);
+        cudaStreamDestroy(plan->side);
+    }
+    for (cudaEvent_t e : plan->ev_order)
+        if (e) cudaEventDestroy(e);
     delete plan;
     return SSE_OK;
 }
@@ -382,28 +388,64 @@ sse_status sse_execute_host(sse_plan_t *plan, const sse_io *h, void *stream) {
     }
     cudaStream_t st = (cudaStream_t)stream;
     char *base = (char *)plan->staging;
-    sse_io dio{};
-    const void **dg[2] = {&dio.G_gt, &dio.G_lt}, **dd[2] = {&dio.D_gt, &dio.D_lt};
-    void **ds[2] = {&dio.S_gt, &dio.S_lt};
+    auto fail = [&](cudaError_t e, const char *what) {
+        cudaStreamSynchronize(st);
+        if (plan->side) cudaStreamSynchronize(plan->side);
+        plan->last_stream = st;
+        return cuda_fail(e, what);
+    };
+    // one sign: copies in, kernels, copies out on the caller's stream.  Both signs: sign 0
+    // on the caller's stream, sign 1 on the plan's side stream, its input copies after sign
+    // 0's (full link bandwidth for the first kernels' inputs), its kernels after sign 0's
+    // (executions of a plan do not overlap), so that sign 1's inputs and sign 0's Sigma
+    // move while the other sign computes
+    const bool both = sgn[0] && sgn[1];
+    if (both && !plan->side) {
+        cudaError_t e = cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            if (!plan->ev_order[k]) e = cudaEventCreateWithFlags(&plan->ev_order[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "create the second stream of sse_execute_host");
+    }
     for (int s = 0; s < 2; ++s) {
         if (!sgn[s]) continue;
+        cudaStream_t ss = (both && s == 1) ? plan->side : st;
         char *g = base + s * (2 * gb + db), *dt = g + gb, *sg = dt + db;
-        cudaError_t e = cudaMemcpyAsync(g, hg[s], gb, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dt, hd[s], db, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "copy inputs to the device");
-        *dg[s] = g;
-        *dd[s] = dt;
-        *ds[s] = sg;
+        cudaError_t e = cudaSuccess;
+        if (both && s == 1) e = cudaStreamWaitEvent(ss, plan->ev_order[0], 0);  // after sign 0's inputs
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g, hg[s], gb, cudaMemcpyHostToDevice, ss);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dt, hd[s], db, cudaMemcpyHostToDevice, ss);
+        if (e == cudaSuccess && both && s == 0) e = cudaEventRecord(plan->ev_order[0], ss);
+        if (e == cudaSuccess && both && s == 1) e = cudaStreamWaitEvent(ss, plan->ev_order[1], 0);  // after sign 0's kernels
+        if (e != cudaSuccess) return fail(e, "copy inputs to the device");
+        sse_io dio{};
+        if (s == 0) {
+            dio.G_gt = g;
+            dio.D_gt = dt;
+            dio.S_gt = sg;
+        } else {
+            dio.G_lt = g;
+            dio.D_lt = dt;
+            dio.S_lt = sg;
+        }
+        const sse_status rs = dispatch(plan, dio, ss);
+        if (rs != SSE_OK) {
+            cudaStreamSynchronize(st);
+            if (plan->side) cudaStreamSynchronize(plan->side);
+            plan->last_stream = st;
+            return rs;
+        }
+        if (both && s == 0) e = cudaEventRecord(plan->ev_order[1], ss);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs[s], sg, gb, cudaMemcpyDeviceToHost, ss);
+        if (e != cudaSuccess) return fail(e, "copy Sigma to the host");
     }
-    sse_status rs = dispatch(plan, dio, st);
-    if (rs != SSE_OK) return rs;
-    for (int s = 0; s < 2; ++s) {
-        if (!sgn[s]) continue;
-        cudaError_t e = cudaMemcpyAsync(hs[s], *ds[s], gb, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_fail(e, "copy Sigma to the host");
+    cudaError_t e = cudaSuccess;
+    if (both) {
+        e = cudaEventRecord(plan->ev_order[2], plan->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, plan->ev_order[2], 0);
     }
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "synchronise after sse_execute_host");
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    plan->last_stream = st;
+    if (e != cudaSuccess) return fail(e, "synchronise after sse_execute_host");
     return SSE_OK;
 }
 

@@ -56,6 +56,10 @@ struct Plan {
     int32_t *d_status = nullptr;      // device status word written by kernels with bounded waits
     void *staging = nullptr;          // device staging of sse_execute_host
     size_t staging_bytes = 0;
+    // sse_execute_host with both signs: a second (non-blocking) stream carries the second
+    // sign, so that its copies overlap the first sign's kernels; events order the two
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_order[3] = {};     // caller stream: inputs of sign 0 copied, sign 0 computed; side stream: done
     cudaStream_t last_stream = nullptr;
     int64_t workspace_bytes = 0;
     // Mixed-path workspace (see sse_mixed.cu), Nkz = 5 tensor-core form: per sign, G
