@@ -1089,7 +1089,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
     using GG = Geo<NK>;
     constexpr int TE = GG::DA_TE;        // energies per tile of this form (rows (k, j, e): 3 NK TE)
     constexpr int kVRows = 3 * NK * TE;  // accumulator rows used
-    constexpr int kPostRows = 3 * TE * NK;  // rows (r', e, k) of a post-product tile: three r'
+    // post-product tiles: rows (r', e, k) for kRpt rows r of the block (four at Nkz <= 3,
+    // where 4 TE Nkz <= 96 rows still leave lane quarter 3 to the encoders), kPT per job
+    constexpr int kRpt = NK <= 3 ? 4 : 3;
+    constexpr int kPT = 12 / kRpt;
+    constexpr int kPostRows = kRpt * TE * NK;
     static_assert(kVRows <= kRowsMax && kPostRows <= kRowsMax, "tile rows");
     // The encoding form (ENC) copies raw G blocks and has the warps of TMEM lane quarter 3
     // encode them for the pre-product; it needs every accumulator and post-product row in
@@ -1402,7 +1406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                         mma_commit(bar_job);
                         // post-product of the job, one M tile at a time as the builders fill it
                         constexpr uint32_t idesc_p = idesc_bf16_f32(kRowsMax, 32);
-                        for (int q = 0; q < kPostTiles && ok; ++q, ++tile_ctr) {
+                        for (int q = 0; q < kPT && ok; ++q, ++tile_ctr) {
                             if (!(ok = mbar_wait_bounded(bar_apost, tile_ctr & 1, kWaitNs))) break;
                             tc_fence_after();
                             const uint32_t dp = tmem + ((tile_ctr & 1) ? kTcPost1 : kTcPost0);
@@ -1607,7 +1611,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     const int srl = row / (TE * NK), se = (row / NK) % TE, sk = row % NK;
                     if (pend_E0 + se >= d.ne) continue;
                     const size_t idx = (((size_t)sk * d.ne + pend_E0 + se) * d.na + a) * kCh +
-                                       (3 * (kPostTiles - kStgTiles + tl) + srl) * 12 + c;
+                                       (kRpt * (kPT - kStgTiles + tl) + srl) * 12 + c;
                     if (!SSE_BC(idx, (long long)d.nkz * d.ne * d.na * kCh, prm.status)) continue;
                     const float *sp = stg + ((size_t)tl * kPostRows + row) * kStgStride + 2 * c;
                     const float2 v = make_float2(sp[0], sp[1]);
@@ -1748,15 +1752,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                     // Tile q: its A is built once the MMAs of tile q - 1 are done (one A buffer);
                     // the accumulator columns it needs are loaded before that wait, and tile
                     // q - 1's result is drained and added to Sigma after tile q is handed to the MMAs.
-                    for (int q = 0; q <= kPostTiles; ++q) {
+                    for (int q = 0; q <= kPT; ++q) {
                         const int tq = tile_ctr + q;  // CTA-wide index of tile q
                         uint32_t vr[12], vi[12];
-                        if (q < kPostTiles) {
-                            const uint32_t ta = tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)((3 * q + arl) * 12);
+                        uint32_t xr[4], xi[4];  // kRpt = 4: row r' = 3, columns t in [4 arl, 4 arl + 4)
+                        if (q < kPT) {
+                            const uint32_t ta = tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)((kRpt * q + arl) * 12);
                             tmem_ld8(ta, *reinterpret_cast<uint32_t(*)[8]>(vr));
                             tmem_ld4(ta + 8, *reinterpret_cast<uint32_t(*)[4]>(vr + 8));
                             tmem_ld8(ta + kTcAccIm, *reinterpret_cast<uint32_t(*)[8]>(vi));
                             tmem_ld4(ta + kTcAccIm + 8, *reinterpret_cast<uint32_t(*)[4]>(vi + 8));
+                            if constexpr (kRpt == 4) {
+                                const uint32_t tb = tmem + ((uint32_t)(aq * 32) << 16) + (uint32_t)((kRpt * q + 3) * 12 + 4 * arl);
+                                tmem_ld4(tb, xr);
+                                tmem_ld4(tb + kTcAccIm, xi);
+                            }
                         }
                         if (q > 0) {
                             // MMAs of tile q - 1 done: its result can be drained, the A tile reused
@@ -1764,11 +1774,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tc_fence_after();
                         }
                         tmem_ld_wait();
-                        if (q < kPostTiles) {
+                        if (q < kPT) {
                             tmem_pin(vr);
                             tmem_pin(vi);
+                            if constexpr (kRpt == 4) {
+                                tmem_pin(xr);
+                                tmem_pin(xi);
+                            }
                         }
-                        if (q < kPostTiles && am < kVRows) {
+                        if (q < kPT && am < kVRows) {
                             // ---- A tile q: rows (r', e, k), K = (j, t, re/im), bf16 hi / lo ----
                             const int row = arl * (TE * NK) + ae * NK + ak;
                             uint8_t *rbase = sApost + (row >> 3) * kPostSbo + (row & 7) * 16;
@@ -1790,9 +1804,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                                 *(uint4 *)(rbase + 9 * 128) = make_uint4(0u, 0u, 0u, 0u);
                                 *(uint4 *)(rbase + 9 * 128 + kPostAPlane) = make_uint4(0u, 0u, 0u, 0u);
                             }
+                            if constexpr (kRpt == 4) {
+                                // row r' = 3 of the tile: this thread's K chunk (j, t in [4 arl, 4 arl + 4))
+                                const int row3 = 3 * (TE * NK) + ae * NK + ak;
+                                uint8_t *rb3 = sApost + (row3 >> 3) * kPostSbo + (row3 & 7) * 16;
+                                uint32_t hw[4], lw[4];
+#pragma unroll
+                                for (int x = 0; x < 4; ++x) {
+                                    const uint2 hl = split2_bf16(__uint_as_float(xr[x]), __uint_as_float(xi[x]));
+                                    hw[x] = hl.x;
+                                    lw[x] = hl.y;
+                                }
+                                uint8_t *p3 = rb3 + (aj * 3 + arl) * 128;
+                                *(uint4 *)p3 = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                                *(uint4 *)(p3 + kPostAPlane) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                                if (aj == 2 && arl == 0) {
+                                    *(uint4 *)(rb3 + 9 * 128) = make_uint4(0u, 0u, 0u, 0u);
+                                    *(uint4 *)(rb3 + 9 * 128 + kPostAPlane) = make_uint4(0u, 0u, 0u, 0u);
+                                }
+                            }
                         }
                         tc_fence_before();
-                        if (q < kPostTiles) {
+                        if (q < kPT) {
                             fence_proxy_async_smem();
                             mbar_arrive(bar_apost);
                         }
@@ -1806,10 +1839,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                             tmem_pin(pv);
                             tc_fence_before();
                         }
-                        if (q > 0 && stg && q - 1 >= kPostTiles - kStgTiles) {
+                        if (q > 0 && stg && q - 1 >= kPT - kStgTiles) {
                             // staged: added to Sigma during the next job (see flush)
                             if (drow < kPostRows) {
-                                float *sp = stg + ((size_t)(q - 1 - (kPostTiles - kStgTiles)) * kPostRows + drow) * kStgStride + 8 * dsub;
+                                float *sp = stg + ((size_t)(q - 1 - (kPT - kStgTiles)) * kPostRows + drow) * kStgStride + 8 * dsub;
                                 *(float4 *)sp = make_float4(pv[0], pv[1], pv[2], pv[3]);
                                 *(float4 *)(sp + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
                             }
@@ -1824,11 +1857,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
                                 else slot_add(dst + s2, v);
                             }
                         }
-                        if (q < kPostTiles)
-                            dst = S + (((size_t)dk * d.ne + (dlive ? E0 + de : 0)) * d.na + a) * kCh + (3 * q + drl) * 12 +
+                        if (q < kPT)
+                            dst = S + (((size_t)dk * d.ne + (dlive ? E0 + de : 0)) * d.na + a) * kCh + (kRpt * q + drl) * 12 +
                                   4 * dsub;
                     }
-                    tile_ctr += kPostTiles;
+                    tile_ctr += kPT;
                     if (stg) {
                         builders_sync<ENC>();  // the staged tiles are complete
                         pend = true;
