@@ -164,10 +164,34 @@ class ClockSampler:
 
 # --- profile-derived traffic -------------------------------------------------------------
 
+def strip_comments(src):
+    """C/C++/CUDA source without its comments and blank lines (string literals kept), so that
+    a comment-only edit leaves a kernel's digest unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+
+
 def source_digest(paths):
     h = hashlib.sha256()
     for p in paths:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        h.update(strip_comments(open(os.path.join(ROOT, p), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,4 +1,4 @@
-// Mixed-precision tensor-core form of the electron scattering self-energy (Eq. 3).
+// Mixed-precision tensor-core forms of the electron scattering self-energy (Eq. 3).
 //
 // Regrouping used here (exact by linearity; Section 3 "Dataflow Optimizations" removes
 // the (qz, w)-independent products from the correlation in the same spirit):
@@ -7,21 +7,23 @@
 //   Sigma[k, E] += sum_j V_j[k, E] . dH_j^dagger                (reduced over slots in FP64)
 // The correlation is the dominant work.  It runs on the tensor cores (tcgen05, kind::f16)
 // as a Toeplitz-in-E, circulant-in-k contraction (the matrix form of Section 3's nested
-// map substitution):
-//   rows m = (e, k, j) of a tile of TE energies (3 * Nkz * TE <= 128),
-//   K     = (energy slot E' of the tile's window, i, k', re/im of X),
-//   N     = the 144 channels (r, t) of a 12 x 12 block,
-// with two TMEM accumulators (real and imaginary part of V).  A holds the Toeplitz
-// operand built from the folded Dt, B the X slices.  Both are split into bf16 hi + lo
-// and contracted as hi*hi + hi*lo + lo*hi with FP32 accumulation; the products
-// dH_i . G and V . dH^dagger run in FP32 on the CUDA cores; the sum over neighbour slots
-// is FP64.  G blocks arrive by bulk (TMA) copies into shared memory.
+// map substitution): rows (k, j, e) of a tile of energies, K = (energy slot E' of the
+// tile's window, i, k', re/im), N = the 144 channels (r, t) of a 12 x 12 block, two TMEM
+// accumulators (Re V, Im V).  Operands are split into bf16 hi + lo and contracted as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation; each slot's FP32 result is added into
+// Sigma in FP64 for complex128 output.
 //
-// Structure of one CTA (sign, atom a, range of tiles): for every (tile, slot) "job",
-// stream the tile's window of energy slots in stages (double-buffered): convert the
-// stage's G blocks, build the X slices and the Toeplitz slice in shared memory, issue the
-// MMAs from one thread and let them run while the next stage is built; at the end of the
-// job, drain the accumulators and apply dH_j^dagger.
+// Two kernels:
+// - sse_tc_kernel (warp-specialised, every Nkz <= 5 when its tiles fit in shared memory):
+//   the Toeplitz operand read in place from a per-(atom, slot) table by shifting the
+//   descriptor, both small products (dH_i . G and V . dH_j^dagger) on the tensor cores too,
+//   roles split over 16 warps (operand builders, three MMA-issuing lanes, a bulk-copy lane;
+//   below Nkz = 5 the warps of TMEM lane quarter 3 encode raw G blocks for the pre-product);
+//   fed by the workspace pass (sse_split_g_kernel at Nkz = 5, sse_slot_tables_kernel).
+// - sse_mixed_kernel (single role, no workspace; sse_execute_noalloc, large Nw): one CTA
+//   converts the stage's G blocks, builds X and the Toeplitz slice in shared memory with
+//   FP32 CUDA-core products, issues the MMAs from one thread while the next stage is built,
+//   and applies dH_j^dagger in FP32 on the CUDA cores at the end of each job.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdlib.h>
@@ -202,7 +204,7 @@ template <typename CT>
 __global__ void __launch_bounds__(256) sse_split_g_kernel(const CT *__restrict__ G, uint8_t *__restrict__ ws,
                                                           int ne, int na, int nkz) {
     __shared__ float2 sg[5 * kCh];  // G[k', E', f] of the slice (Nkz = 5), read contiguously
-    if (nkz > 5) return;           // the tensor-core form serves Nkz = 5 only
+    if (nkz > 5) return;           // stored slices serve Nkz = 5 only (below, the kernel encodes G)
     const long long slice = blockIdx.x;
     const int E = (int)(slice / na), f = (int)(slice % na);
     for (int x = threadIdx.x; x < nkz * kCh; x += 256)
@@ -884,8 +886,9 @@ __global__ void __launch_bounds__(kThreads, 1) sse_mixed_kernel(const __grid_con
 // Im V, one the pre-product, so that one issuer's bookkeeping between stages hides behind the
 // others' queued MMAs (an issuing thread blocks while the tensor pipe's queue is full, and its
 // MMAs complete in its own issue order; the three write disjoint accumulators).  The first sits on
-// the scheduler of the three builder warps without stage work (they sleep at a hardware
-// barrier between epilogues).  One bulk-copy warp streams the G
+// the scheduler of the three builder warps without stage work (lane quarter 3: at Nkz = 5
+// they add the previous job's staged post-product results into Sigma; below Nkz = 5 they
+// are the encoders, and the Re-side issuer and the bulk-copy lane swap warps).  One bulk-copy warp streams the G
 // slices into a ring and the slot tables into shared memory.  Hand-offs go through
 // mbarriers: builders -> control "B of stage g built", "post-product tile built"; control
 // -> builders through MMA commits ("X of a pair ready", "B buffer free", "job accumulated");
@@ -909,15 +912,15 @@ constexpr uint32_t kTcPost0 = 320, kTcPost1 = 352;  // post-product accumulators
 constexpr uint32_t kTcPre = 384;               // X of a pair of stages, 2 x 64 columns
 constexpr int kDhJ = 160;    // float2 per direction j of the padded dH copy
 // Post-product Sigma_slot[(e, k), r, s] = sum_{j, t} V_j[(e, k)][r, t] conj(dH_j[s, t]) on the
-// tensor cores: rows (r', e, k) of an M tile (three rows r per tile, four tiles), K = (j, t,
-// re/im of V) = 72 padded to 80, N = (s, re/im of the product) = 24 padded to 32.
+// tensor cores: rows (r', e, k) of an M tile (three rows r per tile, four tiles; four rows
+// and three tiles at Nkz <= 3), K = (j, t, re/im of V) = 72 padded to 80, N = (s, re/im of
+// the product) = 24 padded to 32.
 constexpr int kPostK = 80, kPostKc = kPostK / 8;            // K and its 16-byte chunks
 constexpr uint32_t kPostSbo = kPostKc * 128;                // bytes between 8-row groups
 constexpr uint32_t kPostAPlane = (kRowsMax / 8) * kPostSbo;  // 20480
 constexpr uint32_t kPostBPlane = (32 / 8) * kPostSbo;        // 5120
 constexpr int kTcBarBytes = 256;  // 24 mbarriers, the TMEM address and the flags; the unit index follows
 constexpr int kTcEncoders = 96;   // encoding form: the warps of TMEM lane quarter 3 (3, 7, 11)
-constexpr int kPostTiles = 4;     // post-product M tiles per job (three rows r of the block each)
 // Nkz = 5: the results of the job's last kStgTiles post-product tiles are staged in shared
 // memory (rows of kStgStride floats: 24 values and padding against bank conflicts) and
 // added to Sigma by the builder warps without stage work during the next job
@@ -1732,7 +1735,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sse_tc_kernel(const __grid_cons
 
                 if (job_last) {
                     // ---- epilogue of the job: Sigma += sum_j V_j dH_j^dagger (V = acc_re + i acc_im) ----
-                    // the X warps see the job's MMAs done; the others (no stage work) sleep at the
+                    // the X warps see the job's MMAs done; the others (no stage work) wait at the
                     // barrier until then
                     if (xw) bwait(bar_job, job_ctr & 1);
                     ++job_ctr;
